@@ -1,0 +1,116 @@
+"""The whole oracle scheme against the paper's accuracy tables and exact solutions.
+
+Tables 1-4 (Sec. 3, Examples 1-4) print L-infinity and L1 errors; the oracle
+reproduces them within a stated factor under the readings of the time step
+(dt = 0.6 dx^{5/3} / alpha for convergence studies), of alpha (local in 1D,
+grid-wide in 2D) and of the L1 norm (dx * sum in 1D, mean in 2D).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import exact
+import oracle
+from paper_1909_13263_gb300 import inputs
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+TF = 0.5 / math.pi**2
+
+
+def _table(name):
+    rows = {}
+    for line in open(os.path.join(GOLD, name)):
+        if line.startswith("#") or not line.strip():
+            continue
+        v = line.split()
+        rows[int(v[0])] = {"arclength": (float(v[1]), float(v[2])), "jp": (float(v[3]), float(v[4]))}
+    return rows
+
+
+def _run_1d(ham, n, weights, t_final, exact_fn, alpha_mode="local_lagged"):
+    x, dx = inputs.axis(n, -1.0, 1.0, "periodic")
+    cfg = oracle.make_cfg(dim=1, nx=n, dx=dx, ham=ham, weights=weights, dt_mode="dx53", alpha_mode=alpha_mode)
+    phi, steps, t, _, st = oracle.solve(cfg, inputs.phi0_negcos_1d(x), t_final)
+    assert st == 0 and t == t_final
+    e = np.abs(phi - exact_fn(x))
+    return e.max(), dx * e.sum()
+
+
+def _run_2d(ham, n, weights, alpha_mode="global_lagged"):
+    x, dx = inputs.axis(n, -2.0, 2.0, "periodic")
+    cfg = oracle.make_cfg(dim=2, nx=n, ny=n, dx=dx, ham=ham, weights=weights, dt_mode="dx53",
+                          alpha_mode=alpha_mode)
+    phi, steps, t, _, st = oracle.solve(cfg, inputs.phi0_negcos_diag_2d(x, x), TF)
+    assert st == 0 and t == TF
+    e = np.abs(phi - exact.negcos_diag_2d(ham, x, x, TF))
+    return e.max(), e.mean()
+
+
+def _check(errs, table, weights, factor, factor_l1=None):
+    factor_l1 = factor if factor_l1 is None else factor_l1
+    for n, (linf, l1) in errs.items():
+        p_linf, p_l1 = table[n][weights]
+        assert p_linf / factor < linf < p_linf * factor, (n, linf, p_linf)
+        assert p_l1 / factor_l1 < l1 < p_l1 * factor_l1, (n, l1, p_l1)
+
+
+@pytest.mark.parametrize("weights", ["arclength", "jp"])
+def test_table1_linear_advection(weights):
+    tab = _table("table1_ex1_advection.txt")
+    errs = {n: _run_1d("advect1d", n, weights, 2.0, lambda x: -np.cos(np.pi * (x - 2.0)))
+            for n in (20, 40, 80, 160)}
+    _check(errs, tab, weights, 1.6)
+    orders = [math.log2(errs[n][0] / errs[2 * n][0]) for n in (40, 80)]
+    assert min(orders) > 4.8
+
+
+@pytest.mark.parametrize("weights", ["arclength", "jp"])
+def test_table2_negcos_1d(weights):
+    tab = _table("table2_ex2_negcos1d.txt")
+    errs = {n: _run_1d("negcos1d", n, weights, TF, lambda x: exact.negcos_1d("negcos1d", x, TF))
+            for n in (20, 40, 80, 160, 320)}
+    _check(errs, tab, weights, 1.3)
+
+
+def test_table2_needs_local_alpha():
+    # the grid-wide alpha is 2-5x too dissipative for Table 2: pins the local reading in 1D
+    tab = _table("table2_ex2_negcos1d.txt")
+    linf, _ = _run_1d("negcos1d", 80, "arclength", TF, lambda x: exact.negcos_1d("negcos1d", x, TF),
+                      alpha_mode="global_lagged")
+    assert linf > 2.5 * tab[80]["arclength"][0]
+
+
+@pytest.mark.parametrize("weights", ["arclength", "jp"])
+@pytest.mark.parametrize("ham,table", [("burgers2d", "table3_ex3_burgers2d.txt"),
+                                       ("negcos2d", "table4_ex4_negcos2d.txt")])
+def test_tables3_4_two_dimensional(ham, table, weights):
+    tab = _table(table)
+    errs = {n: _run_2d(ham, n, weights) for n in (20, 40, 80)}
+    # the 2D L1 normalisation is not stated: the mean of |e| is within 2.5x, dx*dy*sum is not
+    _check(errs, tab, weights, 2.0, 2.5)
+
+
+def test_burgers_1d_smooth_fifth_order():
+    # Example 6 before the kink forms: order close to 5 against characteristics
+    ex = lambda x: exact.negcos_1d("burgers1d", x, TF)
+    e = [_run_1d("burgers1d", n, "arclength", TF, ex)[0] for n in (80, 160, 320)]
+    orders = [math.log2(e[i] / e[i + 1]) for i in range(2)]
+    assert orders[-1] > 4.5, orders
+
+
+@pytest.mark.parametrize("weights", ["arclength", "jp"])
+def test_burgers_1d_kink_is_non_oscillatory(weights):
+    # Example 6 at t = 3.5/pi^2: a kink has formed; the solution stays bounded by the
+    # Hopf-Lax bounds (no new extrema above max phi0 or below min phi0 - t max H)
+    n = 80
+    x, dx = inputs.axis(n, -1.0, 1.0, "periodic")
+    cfg = oracle.make_cfg(dim=1, nx=n, dx=dx, ham="burgers1d", weights=weights, alpha_mode="local_lagged")
+    tk = 3.5 / math.pi**2
+    phi, _, t, _, st = oracle.solve(cfg, inputs.phi0_negcos_1d(x), tk)
+    assert st == 0 and np.all(np.isfinite(phi))
+    # phi_t = -(phi_x+1)^2/2 <= 0: phi never increases; and the kink stays a corner
+    assert phi.max() <= 1.0 + 1e-12
+    d2 = np.diff(phi, 2)
+    assert np.sum(np.abs(np.diff(np.sign(d2[np.abs(d2) > 1e-3]))) > 0) <= 6
