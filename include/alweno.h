@@ -1,0 +1,202 @@
+/*
+ * alweno.h -- C ABI of the GB300 arc-length WENO (WENO-L) solver for
+ * Hamilton-Jacobi equations  phi_t + H(D phi) = 0  (paper: "Arc length based
+ * WENO scheme for Hamilton-Jacobi Equations", Sec. 2, Steps 1-5).
+ *
+ * One call advances phi with the fifth-order WENO reconstruction of the
+ * one-sided derivatives phi_x^-/+ (Steps 1-2), nonlinear weights from the
+ * arc-length smoothness indicators (Step 4, Eq. newbeta/length) or the
+ * Jiang-Peng indicators (the comparison scheme of Sec. 3), the
+ * Lax-Friedrichs numerical Hamiltonian (Sec. 2, LF flux) and the TVD-RK3
+ * time integrator (Step 5), in 1D or 2D (dimension by dimension, Sec. 2 Note).
+ * Every RK stage is one CUDA kernel on the device.
+ *
+ * Conventions (all entry points):
+ *  - Return an alw_status; nothing aborts or throws across the ABI.  On error,
+ *    alw_last_error() returns a thread-local message.
+ *  - Host pointers passed in are owned by the caller and only read (or
+ *    written, for outputs) during the call.
+ *  - Device memory is owned by the library.  It is obtained through the
+ *    allocator installed with alw_set_allocator (default: the CUDA
+ *    stream-ordered allocator on the solver's stream).
+ *  - Arrays are row-major with x fastest: index j*nx + i for node (x_i, y_j);
+ *    1D arrays have ny = 1.
+ *  - There is no CPU fallback: without a usable CUDA device every call that
+ *    needs one returns ALW_ECUDA.
+ */
+#ifndef ALWENO_H
+#define ALWENO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ALW_OK = 0,
+  ALW_EINVAL = 1,      /* bad argument (size mismatch, unknown enum, NULL) */
+  ALW_ENOMEM = 2,      /* device or host allocation failed */
+  ALW_ECUDA = 3,       /* CUDA runtime/driver error */
+  ALW_ENONFINITE = 4,  /* a NaN/Inf appeared in dH/dp during a stage */
+  ALW_ETIMEOUT = 5,    /* a bounded device wait gave up */
+  ALW_EBUSY = 6,       /* object in use (e.g. server still running) */
+  ALW_EBUDGET = 7,     /* request exceeds the device-memory budget */
+  ALW_ENOTFOUND = 8    /* unknown instance / request id */
+} alw_status;
+
+/* Boundary conditions.  PERIODIC: n nodes on [lo, hi), dx = (hi-lo)/n.
+ * LINEXTRAP: n nodes on [lo, hi] including both ends, dx = (hi-lo)/(n-1),
+ * ghost values phi_{-m} = (1+m) phi_0 - m phi_1 (mirror image at the right). */
+enum { ALW_BC_PERIODIC = 0, ALW_BC_LINEXTRAP = 1 };
+
+/* Hamiltonians H(p, q), p = phi_x, q = phi_y (Sec. 3 examples). */
+enum {
+  ALW_H_BURGERS2D = 0, /* (p+q+1)^2/2     Example 3 */
+  ALW_H_NEGCOS2D = 1,  /* -cos(p+q+1)     Example 4 */
+  ALW_H_SIN2D = 2,     /* sin(p+q)        Example 10 */
+  ALW_H_ADVECT1D = 3,  /* p               Example 1 */
+  ALW_H_BURGERS1D = 4, /* (p+1)^2/2       Example 6 */
+  ALW_H_NEGCOS1D = 5,  /* -cos(p+1)       Example 2 */
+  ALW_H_EIKONAL2D = 6  /* sqrt(p^2+q^2+1) Example 12 */
+};
+
+/* Smoothness indicators of the nonlinear weights (Step 4). */
+enum { ALW_W_ARCLEN = 0, ALW_W_JP = 1 };
+
+/* alpha of the Lax-Friedrichs flux (LF flux, alpha = max |H_1|) and of the
+ * CFL time step.  A "grid maximum" is the maximum over all nodes and over the
+ * four (u^-/u^+, v^-/v^+) combinations of |dH/dp| (x) and |dH/dq| (y).
+ *  LOCAL_*  : flux uses the node's own maximum over the four combinations.
+ *  GLOBAL_* : flux uses a grid maximum.
+ *  *_LAGGED : the grid maximum of the previous stage (one kernel per stage;
+ *             a prime pass over phi^0 supplies the first).
+ *  *_EXACT  : the grid maximum of the current stage (GLOBAL) / of phi^n for
+ *             dt (both): an extra reduction pass, for validation.
+ *  FIXED    : alpha_fixed for flux and dt.
+ *  DEFAULT  : LOCAL_LAGGED in 1D, GLOBAL_LAGGED in 2D. */
+enum {
+  ALW_ALPHA_DEFAULT = -1,
+  ALW_ALPHA_LOCAL_LAGGED = 0,
+  ALW_ALPHA_LOCAL_EXACT = 1,
+  ALW_ALPHA_GLOBAL_LAGGED = 2,
+  ALW_ALPHA_GLOBAL_EXACT = 3,
+  ALW_ALPHA_FIXED = 4
+};
+
+/* Time step (Sec. 3: CFL 0.6): dt = cfl / (alpha_x/lx + alpha_y/ly) with
+ * lx = dx (CFL) or dx^{5/3} (DX53, for convergence studies); the last step is
+ * clipped so that t reaches t_final exactly. */
+enum { ALW_DT_CFL = 0, ALW_DT_DX53 = 1 };
+
+/* Arithmetic.  FP64: all in double.  FP32: phi and all arithmetic in float.
+ * MIXED: stencil arithmetic in float; phi^n is held as an unevaluated sum of
+ * two floats (hi + lo, about 48 significant bits) and the RK stages store
+ * float increments phi_s - phi^n, so the accumulation of phi over long runs
+ * keeps double-class precision; the CFL reduction is in double. */
+enum { ALW_PREC_FP64 = 0, ALW_PREC_FP32 = 1, ALW_PREC_MIXED = 2 };
+
+typedef struct {
+  int32_t dim;          /* 1 or 2 */
+  int32_t nx, ny;       /* nodes per direction; ny = 1 when dim = 1 */
+  int32_t bc;           /* ALW_BC_* (same on every side) */
+  double xlo, xhi;      /* x extent */
+  double ylo, yhi;      /* y extent (ignored when dim = 1) */
+} alw_grid;
+
+typedef struct {
+  int32_t kind;         /* ALW_H_* */
+  double param[4];      /* reserved, must be zero */
+} alw_hamiltonian;
+
+typedef struct {
+  int32_t weights;      /* ALW_W_* */
+  double eps;           /* epsilon of Eq. WLOC1 (paper: 1e-6) */
+  double cfl;           /* CFL number (paper: 0.6) */
+  int32_t dt_mode;      /* ALW_DT_* */
+  int32_t alpha_mode;   /* ALW_ALPHA_* */
+  double alpha_fixed[2];/* used by ALW_ALPHA_FIXED */
+  int32_t precision;    /* ALW_PREC_* */
+} alw_scheme;
+
+/* Checkpoint: phi^n is transferred separately (alw_get_phi / alw_set_state). */
+typedef struct {
+  double t;             /* current time */
+  int64_t steps;        /* RK3 steps taken */
+  double alpha[2];      /* most recent grid-maximum reduction (lagged alpha) */
+} alw_state;
+
+typedef struct alw_solver alw_solver;
+
+/* Device allocator hook (process-wide).  alloc returns device memory of at
+ * least `bytes` usable in stream order on `stream`, or NULL; free releases it.
+ * Pass NULL to restore the default (cudaMallocAsync/cudaFreeAsync). */
+typedef struct {
+  void *(*alloc)(size_t bytes, void *stream, void *ctx);
+  void (*free)(void *ptr, size_t bytes, void *stream, void *ctx);
+  void *ctx;
+} alw_allocator;
+alw_status alw_set_allocator(const alw_allocator *allocator);
+
+/* Library version string and the thread-local message of the last error. */
+const char *alw_version(void);
+const char *alw_last_error(void);
+
+/* Create a solver on the current CUDA device; `cuda_stream` is a cudaStream_t
+ * (NULL = the default stream) on which every later call enqueues its work.
+ * Problem statement: Eq. HJ / HJ1.  Errors: ALW_EINVAL (bad grid/scheme, nx <
+ * 1, LINEXTRAP with fewer than 2 nodes, 1D grid with a 2D Hamiltonian or the
+ * reverse), ALW_ENOMEM, ALW_ECUDA. */
+alw_status alw_create(const alw_grid *grid, const alw_hamiltonian *ham, const alw_scheme *scheme,
+                      void *cuda_stream, alw_solver **out);
+alw_status alw_destroy(alw_solver *s);
+
+/* Set phi(., 0) from a host array of n = nx*ny doubles (copied); resets t to
+ * 0, the step count and the lagged alpha.  ALW_EINVAL if n != nx*ny. */
+alw_status alw_set_phi0(alw_solver *s, const double *host_phi, size_t n);
+
+/* Same from a device array (e.g. a torch tensor's data pointer) of n values of
+ * `dtype` (0 = double, 1 = float), contiguous row-major; copied on the stream. */
+alw_status alw_set_phi0_device(alw_solver *s, const void *dev_phi, int32_t dtype, size_t n);
+
+/* Advance to t_final with TVD-RK3 (Step 5): whole steps, the last one clipped.
+ * Work is enqueued as CUDA-graph replays on the solver's stream; the call
+ * returns after the device reports t >= t_final.  steps_out (nullable) gets
+ * the number of steps taken by this call.  ALW_ENONFINITE if dH/dp became
+ * non-finite (phi is left at the step where it was detected). */
+alw_status alw_step_to(alw_solver *s, double t_final, int64_t *steps_out);
+
+/* Advance exactly nsteps RK3 steps with the CFL time step (no clipping; used
+ * for throughput measurement).  Asynchronous: returns after enqueueing. */
+alw_status alw_advance(alw_solver *s, int64_t nsteps);
+
+/* Run a single RK stage (1, 2 or 3) with the given dt, for stage-level tests.
+ * Stage 1 reads phi^n and writes stage 1's state, and so on; the state after
+ * stage 3 is phi^{n+1} (t and the step count are not changed). */
+alw_status alw_run_stage(alw_solver *s, int32_t stage, double dt);
+
+/* Wait for the solver's stream; returns ALW_ENONFINITE if flagged. */
+alw_status alw_sync(alw_solver *s);
+
+/* Copy phi (interior, n = nx*ny doubles) to a caller-owned host buffer.
+ * For MIXED the two float parts are summed exactly in double. */
+alw_status alw_get_phi(alw_solver *s, double *host_out, size_t n);
+alw_status alw_get_phi_device(alw_solver *s, void *dev_out, int32_t dtype, size_t n);
+
+/* Read the state of RK stage `stage` (1 or 2) after alw_run_stage (phi_1 or
+ * phi_2 in the notation of Step 5), as doubles. */
+alw_status alw_get_stage_phi(alw_solver *s, int32_t stage, double *host_out, size_t n);
+
+/* Time, steps, lagged alpha; and restoring them with phi (checkpoint/resume:
+ * resuming reproduces an uninterrupted run bit for bit). */
+alw_status alw_get_state(alw_solver *s, alw_state *state);
+alw_status alw_set_state(alw_solver *s, const alw_state *state, const double *host_phi, size_t n);
+
+/* Device bytes held by the solver. */
+alw_status alw_memory_bytes(alw_solver *s, size_t *bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ALWENO_H */

@@ -1,0 +1,32 @@
+// Launcher of the stage kernel for one precision (included once per precision TU).
+#pragma once
+#include "alw_stage.cuh"
+
+namespace alw {
+
+template <int PREC, int DIM, int W>
+static int launch_one(const StageParams &p, cudaStream_t stream) {
+  using Sh = Shape<PREC, DIM>;
+  auto kern = stage_kernel<PREC, DIM, W>;
+  const size_t smem = Sh::smem_bytes();
+  static bool configured = false;   // attribute is per function; setting it twice is harmless
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    configured = true;
+  }
+  dim3 grid(p.tiles_x, p.tiles_y);
+  kern<<<grid, Sh::NT, smem, stream>>>(p);
+  return (int)cudaGetLastError();
+}
+
+template <int PREC>
+static int launch_stage_impl(const StageParams &p, void *stream) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (p.dim == 2) {
+    return p.weights == W_JP ? launch_one<PREC, 2, W_JP>(p, s) : launch_one<PREC, 2, W_ARCLEN>(p, s);
+  }
+  return p.weights == W_JP ? launch_one<PREC, 1, W_JP>(p, s) : launch_one<PREC, 1, W_ARCLEN>(p, s);
+}
+
+}  // namespace alw

@@ -1,0 +1,6 @@
+// Stage-kernel instantiations for one arithmetic variant.
+#include "alw_launch.cuh"
+
+namespace alw {
+int launch_stage_f64(const StageParams &p, void *stream) { return launch_stage_impl<P_F64>(p, stream); }
+}  // namespace alw
