@@ -1,0 +1,354 @@
+#!/usr/bin/env python3
+"""Throughput of the WENO-L hot path on one GB300 (or N replicas under torchrun).
+
+Workload (default): Example 3 of the paper -- phi_t + (phi_x + phi_y + 1)^2/2 = 0
+on [-2, 2)^2 periodic, phi0 = -cos(pi (x + y)/2) -- on an 8192 x 8192 grid,
+arc-length weights, eps = 1e-6, CFL 0.6, Lax-Friedrichs with the lagged grid
+maximum alpha, mixed precision (float stencil, phi^n as two floats, double CFL
+reduction).  One bench step = one TVD-RK3 time step = three fused stage
+kernels.  Metric: point-updates/s = grid nodes x steps / device time.
+
+Also reported: per-stage roofline (the stage kernel), an end-to-end solve to
+t = 0.5/pi^2 through the C ABI with host buffers, clocks sampled during the
+timed region, and the FP64 CPU oracle on a bounded sample (cpu_baseline).
+
+--impl reference times the FP64 CPU oracle instead (bounded samples of the
+same workload per step) and prints the same JSON line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "WENO-AL point-updates/s"
+UNIT = "point-updates/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+MUFU_PER_SM_CLK = 16          # measured: rsqrt / lg2 / rcp.approx throughput per SM per clock
+FP32_LANES_PER_SM = 128
+
+# algorithmic work of one 2D node in one stage (arc-length weights, Burgers H):
+# per direction 3 F evaluations (rsqrt + lg2), 3 interval means (1 reciprocal each),
+# 2 weight sets (1 reciprocal each) -> 11 MUFU ops; FP32 flops ~107 per direction
+# plus ~33 for alpha, H-hat and the RK combination (see the design doc for the count)
+ALGO = {
+    ("arclength", "mixed"): {"mufu": 22, "flops": 250, "bytes": (12, 16, 20)},
+    ("arclength", "fp32"): {"mufu": 22, "flops": 240, "bytes": (8, 12, 12)},
+    ("jp", "mixed"): {"mufu": 4, "flops": 180, "bytes": (12, 16, 20)},
+    ("jp", "fp32"): {"mufu": 4, "flops": 170, "bytes": (8, 12, 12)},
+    ("arclength", "fp64"): {"mufu": 0, "flops": 250, "bytes": (16, 24, 24)},
+}
+
+
+def _kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1909_13263_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                clk, cmax = float(r[1]), float(r[2])
+            except (ValueError, IndexError):
+                continue
+            sm.append(clk)
+            mx = max(mx, cmax)
+            for k, name in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        load = [c for c in sm if c > 0.5 * max(sm)]
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        return json.load(open(PEAKS_FILE)), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def _traffic():
+    """DRAM bytes per stage launch from the committed ncu capture, if the kernel is unchanged."""
+    try:
+        t = json.load(open(TRAFFIC_FILE))
+    except (OSError, ValueError):
+        return None
+    if t.get("source_hash") != _kernel_source_hash():
+        return None
+    return t
+
+
+def cpu_oracle_rate(n: int, steps: int):
+    """FP64 oracle (one core) on an n x n Example-3 grid for `steps` RK3 steps."""
+    import oracle
+    from paper_1909_13263_gb300 import inputs
+
+    x, dx = inputs.axis(n, -2.0, 2.0, "periodic")
+    phi0 = inputs.phi0_negcos_diag_2d(x, x)
+    cfg = oracle.make_cfg(dim=2, nx=n, ny=n, dx=dx, ham="burgers2d", weights="arclength",
+                          alpha_mode="global_lagged")
+    a, _ = oracle.alpha_of(cfg, phi0)
+    dt = 0.6 / (a[0] / dx + a[1] / dx)
+    t0 = time.perf_counter()
+    _, st, _, _, _ = oracle.solve(cfg, phi0, steps * dt * 0.999999, alpha_state=a.copy())
+    el = time.perf_counter() - t0
+    return n * n * st / el, el, st
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    n = args.ref_n
+    rates = []
+    for _ in range(args.warmup):
+        cpu_oracle_rate(n, 1)
+    total_pts, total_t = 0, 0.0
+    for _ in range(args.steps):
+        r, el, st = cpu_oracle_rate(n, 1)
+        total_pts += n * n * st
+        total_t += el
+    value = total_pts / total_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"ex3_burgers2d_{args.n}sq", "sample": f"{n}x{n} grid, 1 RK3 step per bench step",
+                   "weights": "arclength"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"one RK3 step of Example 3 on a {n}x{n} grid per bench step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1909_13263_gb300 import inputs, native
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    native.load()
+    native.use_torch_allocator(True)
+    stream = torch.cuda.Stream()
+    n = args.n
+    x, dx = inputs.axis(n, -2.0, 2.0, "periodic")
+    tf = 0.5 / math.pi**2
+    kw = dict(dim=2, nx=n, ny=n, xlo=-2.0, xhi=2.0, ylo=-2.0, yhi=2.0, ham="burgers2d", weights=args.weights,
+              precision=args.precision, alpha_mode="global_lagged")
+    with torch.cuda.stream(stream):
+        xs = torch.tensor(x, device="cuda", dtype=torch.float64)
+        phi0_dev = -torch.cos(math.pi * (xs[None, :] + xs[:, None]) / 2.0)
+        s = native.Solver(stream=stream, **kw)
+        s.set_phi0(phi0_dev)
+        del phi0_dev
+        s.advance(args.warmup)
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as cs:
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            s.advance(args.steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        s.sync()
+        ms = ev0.elapsed_time(ev1)
+        clocks = cs.summary()
+        # per-stage device time of the stage kernel (events on the launching stream)
+        st = s.get_state()
+        dt = 0.6 / (st.alpha[0] / dx + st.alpha[1] / dx)
+        reps = 5
+        stage_ms = [0.0, 0.0, 0.0]
+        for _ in range(reps):
+            for k in range(3):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                s.run_stage(k + 1, dt)
+                b.record(stream)
+                b.synchronize()
+                stage_ms[k] += a.elapsed_time(b) / reps
+        s.sync()
+        s.close()
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * n * n * args.steps / (ms * 1e-3)
+
+    # end to end: host phi0 -> device -> RK3 solve to t = 0.5/pi^2 -> host phi
+    e2e = None
+    if not args.no_e2e:
+        phi0_host = inputs.phi0_negcos_diag_2d(x, x)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = native.Solver(stream=stream, **kw)
+        s2.set_phi0(phi0_host)
+        nsteps = s2.step_to(tf)
+        phi = s2.get_phi()
+        el = time.perf_counter() - t0
+        s2.close()
+        if ws > 1:
+            t = torch.tensor([el], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": ws * n * n * nsteps / el, "unit": UNIT,
+               "h2d_bytes_per_step": 8 * n * n / nsteps, "d2h_bytes_per_step": 8 * n * n / nsteps,
+               "solve": f"t = 0.5/pi^2 in {nsteps} RK3 steps, {el:.3f} s wall",
+               "finite": bool(np.isfinite(phi).all())}
+        del phi0_host, phi
+
+    if rank != 0:
+        return 0
+    peaks, src = _peaks()
+    algo = ALGO.get((args.weights, args.precision), ALGO[("arclength", "mixed")])
+    pts = n * n
+    stage_total_ms = sum(stage_ms)
+    mufu_achieved = algo["mufu"] * pts * 3 / (stage_total_ms * 1e-3) / 1e9        # Gop/s
+    mufu_peak = SM_COUNT * MUFU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e9
+    bytes_step = sum(algo["bytes"]) * pts
+    hbm_achieved = bytes_step / (stage_total_ms * 1e-3) / 1e9
+    traffic = _traffic()
+    roof = {
+        "kernel": "stage_kernel (3 launches per RK3 step; per-launch average)",
+        "bound": "alu",
+        "unit": "Gop/s",
+        "achieved": mufu_achieved,
+        "peak": mufu_peak,
+        "frac": mufu_achieved / mufu_peak,
+        "peak_source": f"derived: {SM_COUNT} SMs x {MUFU_PER_SM_CLK} MUFU/clk x {SM_MAX_MHZ:.0f} MHz",
+        "traffic": (traffic["dram_bytes_per_point_step"] * pts / 3.0) if traffic else None,
+        "stage_ms": stage_ms,
+        "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": peaks.get("hbm_gbs"),
+                "frac": hbm_achieved / peaks.get("hbm_gbs", 6800.0), "peak_source": src,
+                "algorithmic_bytes_per_point_step": sum(algo["bytes"])},
+        "fp32": {"achieved_tflops": algo["flops"] * pts * 3 / (stage_total_ms * 1e-3) / 1e12,
+                 "peak_tflops": SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12},
+    }
+    cpu = None
+    if not args.no_cpu and ws >= 1:
+        import oracle
+
+        oracle.build()
+        r, el, stp = cpu_oracle_rate(args.cpu_n, args.cpu_steps)
+        cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{stp} RK3 steps of Example 3 on a {args.cpu_n}x{args.cpu_n} grid ({el:.1f} s)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision != "fp64" else "f64", "data": "synthetic",
+        "config": {"workload": f"ex3_burgers2d_{n}sq", "nx": n, "ny": n, "precision": args.precision,
+                   "weights": args.weights, "hamiltonian": "(p+q+1)^2/2", "alpha": "global_lagged",
+                   "step": "one TVD-RK3 step (3 fused stage kernels)",
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{ws}"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--precision", choices=["mixed", "fp32", "fp64"], default="mixed")
+    ap.add_argument("--weights", choices=["arclength", "jp"], default="arclength")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-n", type=int, default=512)
+    ap.add_argument("--cpu-steps", type=int, default=20)
+    ap.add_argument("--ref-n", type=int, default=128)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -171,9 +171,11 @@ alw_status alw_step_to(alw_solver *s, double t_final, int64_t *steps_out);
  * for throughput measurement).  Asynchronous: returns after enqueueing. */
 alw_status alw_advance(alw_solver *s, int64_t nsteps);
 
-/* Run a single RK stage (1, 2 or 3) with the given dt, for stage-level tests.
- * Stage 1 reads phi^n and writes stage 1's state, and so on; the state after
- * stage 3 is phi^{n+1} (t and the step count are not changed). */
+/* Enqueue a single RK stage (1, 2 or 3) with the given dt (asynchronous; for
+ * stage-level tests and per-stage timing).  Stage 1 reads phi^n and writes
+ * stage 1's state, and so on; the state after stage 3 is phi^{n+1} (t and the
+ * step count are not changed).  ALW_EINVAL for a stage outside 1..3 or a
+ * non-finite dt. */
 alw_status alw_run_stage(alw_solver *s, int32_t stage, double dt);
 
 /* Wait for the solver's stream; returns ALW_ENONFINITE if flagged. */

@@ -37,6 +37,7 @@ struct StageParams {
   int tiles_x, tiles_y;  // tile grid
   int dim, bc, ham, weights, alpha_mode, loop_mode;
   int stage;             // 1, 2, 3; 0 = reduction pass only
+  int src_of;            // stage whose source array is read (= stage, or the stage a reduction precedes)
   int read_slot;         // slot holding the alpha this stage uses (flux/dt), -1 none
   int write_slot;        // slot this stage reduces into
   int zero_slot;         // slot the epilogue clears for a later stage, -1 none
@@ -44,6 +45,7 @@ struct StageParams {
   double dx, dy, rdx, rdy, eps;
   double cfl, lx, ly;    // dt = cfl / (ax/lx + ay/ly)
   double alpha_fixed[2];
+  double dt_value;       // LOOP_STAGE: the dt of this stage
   // buffers: padded arrays whose interior origin is at row GY, column GX
   const void *src0, *src1, *src2;  // stencil source (F64/F32: src0; MIXED: hi, lo, delta or null)
   const void *base0, *base1;       // phi^n at the node (F64/F32: base0; MIXED: hi, lo; stage>=2)

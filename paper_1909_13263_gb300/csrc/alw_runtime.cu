@@ -11,8 +11,11 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "../../include/alweno.h"
 #include "alw_internal.h"
+#include "alw_params2d.h"
 
 using namespace alw;
 
@@ -104,6 +107,8 @@ struct alw_solver {
   int g_step_n = 0;
   cudaGraphExec_t g_adv = nullptr;
   bool has_phi = false;
+  bool use2d = false;       // persistent TMA kernel (2D float variants)
+  CUtensorMap maps[6];      // tensor maps of the padded arrays (see Stage2DParams)
 
   void *alloc(size_t bytes) {
     void *p = dev_alloc(bytes, stream);
@@ -121,6 +126,22 @@ int kernel_prec(int precision) {
 }
 
 int launch_stage(const alw_solver *s, const StageParams &p) {
+  if (s->use2d) {
+    Stage2DParams q;
+    memcpy(q.maps, s->maps, sizeof q.maps);
+    q.p = p;
+    const int which = p.stage == 0 ? p.src_of : p.stage;
+    if (s->prec == P_MIXED) {
+      q.map_a = 0;
+      q.map_b = 2;
+      q.map_c = which == 1 ? -1 : (which == 2 ? 4 : 5);
+      return launch_stage2d_mixed(q, s->stream);
+    }
+    q.map_a = which == 1 ? 0 : (which == 2 ? 1 : 2);
+    q.map_b = p.stage >= 2 ? 0 : -1;
+    q.map_c = -1;
+    return launch_stage2d_f32(q, s->stream);
+  }
   switch (s->prec) {
     case P_F64: return launch_stage_f64(p, s->stream);
     case P_F32: return launch_stage_f32(p, s->stream);
@@ -159,6 +180,7 @@ StageParams make_params(const alw_solver *s, int stage, int src_of, int loop_mod
   p.state = s->st;
   p.dt_slot = exact_mode(s->alpha_mode) ? 3 : 2;
   const int which = stage == 0 ? src_of : stage;
+  p.src_of = which;
   if (stage == 0) {
     p.read_slot = -1;
     p.write_slot = 3;
@@ -301,6 +323,35 @@ alw_status prime_alpha(alw_solver *s) {
   return ALW_OK;
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2D float tensor map over a padded array: box = one tile plus halo.
+alw_status make_tensor_map(alw_solver *s, CUtensorMap *m, void *base) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return fail(ALW_ECUDA, "cuTensorMapEncodeTiled is not available");
+  const cuuint64_t dims[2] = {(cuuint64_t)s->pitch, (cuuint64_t)s->rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)s->pitch * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)kBox2DW, (cuuint32_t)kBox2DH};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ALW_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return ALW_OK;
+}
+
 alw_status check_solver(alw_solver *s) {
   if (!s) return fail(ALW_EINVAL, "solver is NULL");
   if (!s->has_phi) return fail(ALW_EINVAL, "phi0 not set");
@@ -383,6 +434,7 @@ alw_status alw_create(const alw_grid *grid, const alw_hamiltonian *ham, const al
   s->pitch = s->tiles_x * tx + 2 * GX;
   s->rows = s->dim == 2 ? s->tiles_y * ty + 2 * GY : 1;
   s->elem = s->prec == P_F64 ? 8 : 4;
+  s->use2d = s->dim == 2 && s->prec != P_F64;
   s->arr_bytes = (size_t)s->pitch * s->rows * s->elem;
 
   auto cleanup = [&](alw_status st) {
@@ -406,6 +458,24 @@ alw_status alw_create(const alw_grid *grid, const alw_hamiltonian *ham, const al
       return cleanup(fail(ALW_ECUDA, "memset failed"));
   }
   if (cudaMemsetAsync(s->st, 0, sizeof(DevState), s->stream) != cudaSuccess) return cleanup(fail(ALW_ECUDA, "memset failed"));
+  if (s->use2d) {
+    memset(s->maps, 0, sizeof s->maps);
+    void *bases[6];
+    int nb;
+    if (s->prec == P_MIXED) {
+      void *b[6] = {s->H[0], s->H[1], s->Lo[0], s->Lo[1], s->D1, s->D2};
+      memcpy(bases, b, sizeof b);
+      nb = 6;
+    } else {
+      void *b[3] = {s->P, s->A, s->B};
+      memcpy(bases, b, sizeof b);
+      nb = 3;
+    }
+    for (int i = 0; i < nb; ++i) {
+      alw_status st = make_tensor_map(s, &s->maps[i], bases[i]);
+      if (st) return cleanup(st);
+    }
+  }
   *out = s;
   return ALW_OK;
 }
@@ -520,16 +590,16 @@ alw_status alw_run_stage(alw_solver *s, int32_t stage, double dt) {
   alw_status st = check_solver(s);
   if (st) return st;
   if (stage < 1 || stage > 3) return fail(ALW_EINVAL, "stage must be 1, 2 or 3");
-  s->h_tf[1] = dt;
-  ALW_CUDA(cudaMemcpyAsync(&s->st->dt, &s->h_tf[1], sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  if (!std::isfinite(dt)) return fail(ALW_EINVAL, "dt must be finite");
   const bool pre = (s->alpha_mode == ALW_ALPHA_GLOBAL_EXACT) || (s->alpha_mode == ALW_ALPHA_LOCAL_EXACT && stage == 1);
   if (pre) {
     ALW_CUDA(cudaMemsetAsync(&s->st->alpha_bits[3][0], 0, 2 * sizeof(unsigned long long), s->stream));
     ALW_LAUNCH(launch_stage(s, make_params(s, 0, stage, LOOP_STAGE)));
   }
-  ALW_LAUNCH(launch_stage(s, make_params(s, stage, stage, LOOP_STAGE)));
+  StageParams p = make_params(s, stage, stage, LOOP_STAGE);
+  p.dt_value = dt;
+  ALW_LAUNCH(launch_stage(s, p));
   if (s->grid.bc == ALW_BC_LINEXTRAP) ALW_LAUNCH(launch_ghosts(ghost_params(s, stage), s->stream));
-  ALW_CUDA(cudaStreamSynchronize(s->stream));
   return ALW_OK;
 }
 

@@ -23,36 +23,6 @@ template <int PREC, int DIM> struct Shape {
   }
 };
 
-// Store one output value at interior node (gi, gj) and at every periodic ghost
-// position that holds a copy of it (a cross-shaped stencil never reads corners).
-template <typename S, int DIM>
-__device__ __forceinline__ void store_node(S *arr, int pitch, int nx, int ny, int bc, int gi, int gj, S val) {
-  const int gy = (DIM == 2) ? GY : 0;
-  S *row = arr + (size_t)(gj + gy) * pitch;
-  row[gi + GX] = val;
-  if (bc != BC_PERIODIC) return;
-  if (gi < 3 || gi >= nx - 3) {
-#pragma unroll
-    for (int k = 1; k <= 3; ++k) {
-      int g = -k, w = ((g % nx) + nx) % nx;
-      if (w == gi) row[g + GX] = val;
-      g = nx - 1 + k;
-      w = g % nx;
-      if (w == gi) row[g + GX] = val;
-    }
-  }
-  if (DIM == 2 && (gj < 3 || gj >= ny - 3)) {
-#pragma unroll
-    for (int k = 1; k <= 3; ++k) {
-      int g = -k, w = ((g % ny) + ny) % ny;
-      if (w == gj) arr[(size_t)(g + GY) * pitch + gi + GX] = val;
-      g = ny - 1 + k;
-      w = g % ny;
-      if (w == gj) arr[(size_t)(g + GY) * pitch + gi + GX] = val;
-    }
-  }
-}
-
 template <int PREC, int DIM, int WEIGHTS>
 __global__ void __launch_bounds__(Shape<PREC, DIM>::NT) stage_kernel(const StageParams p) {
   using S = typename Types<PREC>::S;
@@ -95,6 +65,8 @@ __global__ void __launch_bounds__(Shape<PREC, DIM>::NT) stage_kernel(const Stage
       dt = st->t_final - st->t;
       last = 1;
     }
+  } else if (p.loop_mode == LOOP_STAGE) {
+    dt = p.dt_value;
   } else {
     dt = st->dt;
   }
