@@ -16,6 +16,7 @@
 #pragma once
 #include "alw_device.cuh"
 #include "alw_params2d.h"
+#include "alw_sweep32.cuh"
 #include "alw_tma.cuh"
 
 namespace alw {
@@ -195,80 +196,65 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
     const float *B = A + ARR;
     const float *C = A + 2 * ARR;
 
-    // ---- 1. differences
-    for (int idx = tid; idx < TY * DXW; idx += NT) {
-      const int r = idx / DXW, c = idx - r * DXW;
-      const int i0 = (r + 3) * SW + c + 1, i1 = i0 + 1;
-      float d;
+    // ---- 1. differences (rows by warp, columns by lane: no division, conflict-free)
+    auto cell_diff = [&](int i0, int i1) -> float {
       if (PREC == P_MIXED) {
-        d = (A[i1] - A[i0]) + ((B[i1] - B[i0]) + (has_delta ? (C[i1] - C[i0]) : 0.0f));
+        return (A[i1] - A[i0]) + ((B[i1] - B[i0]) + (has_delta ? (C[i1] - C[i0]) : 0.0f));
       } else {
-        d = A[i1] - A[i0];
+        return A[i1] - A[i0];
       }
-      dX[r * DXP + c] = d * rdx;
+    };
+    for (int r = warp; r < TY; r += NT / 32) {
+#pragma unroll
+      for (int c = lane; c < DXW; c += 32) {
+        const int i0 = (r + 3) * SW + c + 1;
+        dX[r * DXP + c] = cell_diff(i0, i0 + 1) * rdx;
+      }
     }
-    for (int idx = tid; idx < DYH * TX; idx += NT) {
-      const int r = idx / TX, c = idx - r * TX;
-      const int i0 = r * SW + c + 4, i1 = i0 + SW;
-      float d;
-      if (PREC == P_MIXED) {
-        d = (A[i1] - A[i0]) + ((B[i1] - B[i0]) + (has_delta ? (C[i1] - C[i0]) : 0.0f));
-      } else {
-        d = A[i1] - A[i0];
+    for (int r = warp; r < DYH; r += NT / 32) {
+#pragma unroll
+      for (int c = lane; c < TX; c += 32) {
+        const int i0 = r * SW + c + 4;
+        dY[r * TX + c] = cell_diff(i0, i0 + SW) * rdy;
       }
-      dY[r * TX + c] = d * rdy;
     }
     __syncthreads();
 
     const bool edge = (tx0 < 3) || (tx0 + TX > p.nx - 3) || (ty0 < 3) || (ty0 + TY > p.ny - 3);
+    const int colY = ((warp & 1) << 5) + lane, segY = warp >> 1;
 
     // ---- 2./3. sweeps (one code path for both directions)
 #pragma unroll 1
     for (int dir = 0; dir < 2; ++dir) {
-      float v[K + 5];
-      int col = 0, seg = 0;
-      if (dir == 0) {
-#pragma unroll
-        for (int m = 0; m < K + 5; ++m) v[m] = dX[lane * DXP + K * warp + m];
-      } else {
-        col = ((warp & 1) << 5) + lane;
-        seg = warp >> 1;
-#pragma unroll
-        for (int m = 0; m < K + 5; ++m) v[m] = dY[(K * seg + m) * TX + col];
-      }
-      float dm[K], dp[K];
-      weno_sweep<float, K, W>(v, dir == 0 ? rdx : rdy, dir == 0 ? dx : dy, eps, dm, dp);
-      if (dir == 0) {
-#pragma unroll
-        for (int q = 0; q < K; ++q) su[lane * SUP + K * warp + q] = make_float2(dm[q], dp[q]);
-        __syncthreads();
-        continue;
-      }
-      // node (col, y) of the tile
-#pragma unroll
-      for (int q = 0; q < K; ++q) {
-        const int y = K * seg + q;
-        const int gi = tx0 + col, gj = ty0 + y;
+      const float *vsrc = dir == 0 ? dX + lane * DXP + K * warp : dY + (K * segY) * TX + colY;
+      const int vstride = dir == 0 ? 1 : TX;
+      auto v_at = [&](int m) { return vsrc[m * vstride]; };
+      auto emit = [&](int q, float dmq, float dpq) {
+        if (dir == 0) {
+          su[lane * SUP + K * warp + q] = make_float2(dmq, dpq);
+          return;
+        }
+        // node (colY, y) of the tile: phi_y^-/+ = (dmq, dpq)
+        const int y = K * segY + q;
+        const int gi = tx0 + colY, gj = ty0 + y;
         const bool inside = !edge || (gi < p.nx && gj < p.ny);
-        const float2 u = su[y * SUP + col];
-        const float vmq = dm[q], vpq = dp[q];
+        const float2 u = su[y * SUP + colY];
         float ax, ay;
-        Ham2<H>::alpha(u.x, u.y, vmq, vpq, ax, ay);
+        Ham2<H>::alpha(u.x, u.y, dmq, dpq, ax, ay);
         if (inside) {
-          if (!isfinite(u.x + u.y + vmq + vpq)) bad = true;
+          if (!isfinite(u.x + u.y + dmq + dpq)) bad = true;
           amx = fmaxf(amx, ax);
           amy = fmaxf(amy, ay);
         }
-        if (p.stage == 0 || !inside) continue;
+        if (p.stage == 0 || !inside) return;
         const float aX = local_alpha ? ax : fax, aY = local_alpha ? ay : fay;
-        const float Hv = Ham2<H>::value(0.5f * (u.y + u.x), 0.5f * (vpq + vmq));
-        const float L = -((Hv - aX * 0.5f * (u.y - u.x)) - aY * 0.5f * (vpq - vmq));
-        const int sidx = (y + 3) * SW + col + 4;
+        const float Hv = Ham2<H>::value(0.5f * (u.y + u.x), 0.5f * (dpq + dmq));
+        const float L = fmaf(aX * 0.5f, u.y - u.x, fmaf(aY * 0.5f, dpq - dmq, -Hv));
+        const int sidx = (y + 3) * SW + colY + 4;
         const size_t g = (size_t)(gj + GY) * p.pitch + gi + GX;
         if (PREC == P_MIXED) {
-          const float dL = dtf * L;
           if (p.stage == 3) {
-            const float d = (2.0f / 3.0f) * (C[sidx] + dL);
+            const float d = (2.0f / 3.0f) * fmaf(dtf, L, C[sidx]);
             float h, l;
             df_add(A[sidx], B[sidx], d, h, l);
             float *oh = reinterpret_cast<float *>(p.mix_hi[cur ^ 1]);
@@ -281,7 +267,7 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
               ol[g] = l;
             }
           } else {
-            const float d = (p.stage == 1) ? dL : 0.25f * (C[sidx] + dL);
+            const float d = (p.stage == 1) ? dtf * L : 0.25f * fmaf(dtf, L, C[sidx]);
             float *o = reinterpret_cast<float *>(p.out0);
             if (edge) store_node<float, 2>(o, p.pitch, p.nx, p.ny, p.bc, gi, gj, d);
             else o[g] = d;
@@ -292,15 +278,17 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
           if (p.stage == 1) {
             outv = fmaf(dtf, L, src);
           } else if (p.stage == 2) {
-            outv = 0.75f * B[sidx] + 0.25f * fmaf(dtf, L, src);
+            outv = fmaf(0.75f, B[sidx], 0.25f * fmaf(dtf, L, src));
           } else {
-            outv = B[sidx] * (1.0f / 3.0f) + (2.0f / 3.0f) * fmaf(dtf, L, src);
+            outv = fmaf(1.0f / 3.0f, B[sidx], (2.0f / 3.0f) * fmaf(dtf, L, src));
           }
           float *o = reinterpret_cast<float *>(p.out0);
           if (edge) store_node<float, 2>(o, p.pitch, p.nx, p.ny, p.bc, gi, gj, outv);
           else o[g] = outv;
         }
-      }
+      };
+      sweep_stream<K, W>(v_at, dir == 0 ? rdx : rdy, 0.5f * (dir == 0 ? dx : dy), eps, emit);
+      if (dir == 0) __syncthreads();
     }
     __syncthreads();  // raw[buf], dX, dY, su are free for the next tile
   }
