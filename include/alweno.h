@@ -198,6 +198,31 @@ alw_status alw_set_state(alw_solver *s, const alw_state *state, const double *ho
 /* Device bytes held by the solver. */
 alw_status alw_memory_bytes(alw_solver *s, size_t *bytes);
 
+/* ------------------------------------------------------------------------
+ * No-allocation entry point (the paper has no counterpart; it serves callers
+ * that cannot obtain device memory on demand, e.g. a framework whose pool
+ * allocator owns all device memory, or a real-time loop that must not
+ * allocate after start-up).
+ *
+ * Advances the caller's device array dev_phi_in (n = nx*ny doubles, row-major,
+ * x fastest) by nsteps TVD-RK3 steps of fixed size dt with the FP64 stage
+ * kernel and writes the result to dev_phi_out (may equal dev_phi_in).  The
+ * scheme must have precision ALW_PREC_FP64.  The working storage is a fixed
+ * 16 MiB device array inside this library (held by every GPU that loads it,
+ * until the process exits); grids whose three padded FP64 copies do not fit
+ * (about 800 x 800 in 2D) are rejected with ALW_EBUDGET.  No device memory is
+ * allocated or freed.
+ *
+ * The first call on a device looks up the array's address and should be made
+ * before any stream capture.  Every call clears the storage it uses; calls
+ * whose GPU work overlaps (e.g. on two streams at once) race on the shared
+ * storage and must be serialised by the caller.  Work is enqueued on
+ * cuda_stream and the call returns after it completes; ALW_ENONFINITE if
+ * dH/dp became non-finite. */
+alw_status alw_step_noalloc(const alw_grid *grid, const alw_hamiltonian *ham, const alw_scheme *scheme,
+                            const double *dev_phi_in, double *dev_phi_out, double dt, int32_t nsteps,
+                            void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

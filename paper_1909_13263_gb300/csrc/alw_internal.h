@@ -77,6 +77,9 @@ constexpr int K1D = 8;
 int tile_x(int prec, int dim);
 int tile_y(int prec, int dim);
 
+// Set the thread-local message returned by alw_last_error().
+void set_last_error(const char *msg);
+
 // Launchers (defined per precision in alw_stage_*.cu); return cudaError_t as int.
 int launch_stage_f64(const StageParams &p, void *stream);
 int launch_stage_f32(const StageParams &p, void *stream);

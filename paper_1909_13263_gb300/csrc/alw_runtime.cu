@@ -76,6 +76,8 @@ void dev_free(void *p, size_t bytes, cudaStream_t s) {
 
 }  // namespace
 
+void alw::set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+
 int alw::tile_x(int prec, int dim) {
   if (dim == 1) return TX1D;
   return prec == P_F64 ? Tile<P_F64>::TX : Tile<P_F32>::TX;

@@ -110,6 +110,8 @@ def load():
             "alw_get_state": (ctypes.c_int, [P, ctypes.POINTER(State)]),
             "alw_set_state": (ctypes.c_int, [P, ctypes.POINTER(State), P, SZ]),
             "alw_memory_bytes": (ctypes.c_int, [P, ctypes.POINTER(SZ)]),
+            "alw_step_noalloc": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Hamiltonian),
+                                                ctypes.POINTER(Scheme), P, P, D, I32, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -264,3 +266,22 @@ class Solver:
         b = ctypes.c_size_t()
         check(self._L.alw_memory_bytes(self._h, ctypes.byref(b)))
         return b.value
+
+
+def step_noalloc(phi_in, phi_out, *, dim: int, nx: int, ny: int = 1, bc: str = "periodic", xlo: float, xhi: float,
+                 ylo: float = 0.0, yhi: float = 1.0, ham: str, weights: str = "arclength", eps: float = 1e-6,
+                 alpha_mode: str = "default", alpha_fixed=(0.0, 0.0), dt: float, nsteps: int = 1, stream=None):
+    """alw_step_noalloc: nsteps FP64 RK3 steps of fixed dt on caller-owned CUDA float64 tensors,
+    using the library's fixed working storage instead of allocating device memory."""
+    L = load()
+    for t in (phi_in, phi_out):
+        if not (t.is_cuda and str(t.dtype) == "torch.float64" and t.is_contiguous() and t.numel() == nx * ny):
+            raise AlwError(EINVAL, "phi_in/phi_out must be contiguous CUDA float64 tensors of nx*ny values")
+    g = Grid(dim, nx, ny if dim == 2 else 1, BC[bc], xlo, xhi, ylo, yhi)
+    h = Hamiltonian(HAM[ham], (ctypes.c_double * 4)(0, 0, 0, 0))
+    s = Scheme(WEIGHTS[weights], eps, 0.6, DT["cfl"], ALPHA[alpha_mode], (ctypes.c_double * 2)(*alpha_fixed),
+               PREC["fp64"])
+    check(L.alw_step_noalloc(ctypes.byref(g), ctypes.byref(h), ctypes.byref(s), ctypes.c_void_p(phi_in.data_ptr()),
+                             ctypes.c_void_p(phi_out.data_ptr()), float(dt), int(nsteps),
+                             ctypes.c_void_p(_stream_handle(stream))))
+    return phi_out
