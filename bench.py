@@ -69,6 +69,19 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(x: float) -> float:
+    """Maximum of a per-rank number over the process group (identity without one)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -245,10 +258,7 @@ def run_ours(args):
                 stage_ms[k] += a.elapsed_time(b) / reps
         s.sync()
         s.close()
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms)
     value = ws * n * n * args.steps / (ms * 1e-3)
 
     # end to end: host phi0 -> device -> RK3 solve to t = 0.5/pi^2 -> host phi
@@ -263,10 +273,7 @@ def run_ours(args):
         phi = s2.get_phi()
         el = time.perf_counter() - t0
         s2.close()
-        if ws > 1:
-            t = torch.tensor([el], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(el)
         e2e = {"value": ws * n * n * nsteps / el, "unit": UNIT,
                "h2d_bytes_per_step": 8 * n * n / nsteps, "d2h_bytes_per_step": 8 * n * n / nsteps,
                "solve": f"t = 0.5/pi^2 in {nsteps} RK3 steps, {el:.3f} s wall",

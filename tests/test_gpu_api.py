@@ -1,0 +1,155 @@
+"""C-ABI behaviour on the GPU: checkpoint/resume, error paths, full-size sampled
+parity in the configuration bench.py times, and 1D / boundary workloads."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from gpucase import Case, rel_err
+from paper_1909_13263_gb300 import inputs, native
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    native.load()
+    native.use_torch_allocator(True)
+    yield
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed"])
+def test_checkpoint_resume_reproduces_uninterrupted_run(precision):
+    case = Case(2, 96, 80, "negcos2d", precision=precision, lo=-2.0, hi=2.0)
+    phi0 = case.field(seed=12, kind="smooth")
+    t1, t2 = 0.01, 0.025
+    with case.solver() as a:
+        a.set_phi0(phi0)
+        a.step_to(t1)
+        state = a.get_state()
+        mid = a.get_phi()
+        a.step_to(t2)
+        full = a.get_phi()
+        steps_full = a.get_state().steps
+    with case.solver() as b:
+        b.set_state(state, mid)
+        b.step_to(t2)
+        resumed = b.get_phi()
+        assert b.get_state().steps == steps_full
+    if precision == "mixed":
+        # the (hi, lo) split of a checkpointed double is canonical up to a tie in rounding
+        assert rel_err(resumed, full) <= 1e-14
+    else:
+        assert np.array_equal(resumed, full)
+
+
+def test_invalid_arguments_are_rejected():
+    with pytest.raises(native.AlwError) as e:
+        native.Solver(dim=2, nx=16, ny=16, xlo=0, xhi=1, ylo=0, yhi=1, ham="burgers1d")
+    assert e.value.status == native.EINVAL
+    with pytest.raises(native.AlwError) as e:
+        native.Solver(dim=2, nx=1, ny=16, bc="linextrap", xlo=0, xhi=1, ylo=0, yhi=1, ham="burgers2d")
+    assert e.value.status == native.EINVAL
+    s = native.Solver(dim=2, nx=16, ny=16, xlo=0, xhi=1, ylo=0, yhi=1, ham="burgers2d")
+    with pytest.raises(native.AlwError) as e:
+        s.set_phi0(np.zeros(15 * 16))
+    assert e.value.status == native.EINVAL
+    with pytest.raises(native.AlwError) as e:
+        s.step_to(1.0)  # phi0 not set
+    assert e.value.status == native.EINVAL
+    with pytest.raises(native.AlwError) as e:
+        s.run_stage(4, 1e-3)
+    assert e.value.status in (native.EINVAL,)
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_non_finite_input_is_reported(precision):
+    case = Case(2, 64, 64, "burgers2d", precision=precision)
+    phi0 = case.field(seed=1, kind="smooth")
+    phi0[10, 20] = np.nan
+    with case.solver() as s:
+        s.set_phi0(phi0)
+        with pytest.raises(native.AlwError) as e:
+            s.step_to(0.05)
+        assert e.value.status == native.ENONFINITE
+
+
+@pytest.mark.parametrize("precision,alpha", [("mixed", "fixed"), ("mixed", "local_lagged"), ("fp64", "fixed")])
+def test_full_size_8192_sampled_stage_parity(precision, alpha):
+    # the bench configuration (Example 3 on 8192^2): one RK stage on the GPU, checked at
+    # sampled nodes (tile corners, grid edges, random interior) against the oracle's per-node L
+    n = 8192
+    x, dx = inputs.axis(n, -2.0, 2.0, "periodic")
+    case = Case(2, n, n, "burgers2d", lo=-2.0, hi=2.0, precision=precision, alpha_mode=alpha,
+                alpha_fixed=(1.0 + math.pi, 1.0 + math.pi))
+    phi0 = np.ascontiguousarray(inputs.phi0_negcos_diag_2d(x, x))
+    dt = 0.6 / (2 * (1.0 + math.pi) / dx)
+    with case.solver() as s:
+        s.set_phi0(phi0)
+        s.run_stage(1, dt)
+        phi1 = s.get_stage_phi(1)
+    rng = np.random.default_rng(8192)
+    pts = [(0, 0), (n - 1, n - 1), (0, n - 1), (n - 1, 0), (63, 31), (64, 32), (8191, 4095), (4096, 8191)]
+    pts += [(int(i), int(j)) for i, j in rng.integers(0, n, size=(600, 2))]
+    cfg = case.cfg()
+    a = np.array(case.alpha_fixed)
+    errs = []
+    for i, j in pts:
+        ref = phi0[j, i] + dt * oracle.point_L(cfg, phi0, i, j, a)
+        errs.append(abs(phi1[j, i] - ref))
+    err = max(errs) / np.abs(phi0).max()
+    tol = 1e-12 if precision == "fp64" else 64 * 2.0**-24
+    assert err <= tol, err
+
+
+@pytest.mark.parametrize("weights", ["arclength", "jp"])
+def test_1d_kink_solve_matches_oracle(weights):
+    # Example 6 at t = 3.5/pi^2 (kink formed) on the paper's 80-node grid, FP64
+    n = 80
+    x, dx = inputs.axis(n, -1.0, 1.0, "periodic")
+    case = Case(1, n, 1, "burgers1d", weights=weights, alpha_mode="default")
+    phi0 = inputs.phi0_negcos_1d(x)
+    tf = 3.5 / math.pi**2
+    ref, steps, _, _, st = oracle.solve(case.cfg(), phi0, tf)
+    with case.solver() as s:
+        s.set_phi0(phi0)
+        assert s.step_to(tf) == steps
+        assert rel_err(s.get_phi(), ref) <= 1e-12
+
+
+def test_riemann_linextrap_mixed_vs_fp64_gpu():
+    # Example 10's non-convex H = sin(p+q) with linear-extrapolation boundaries on 256^2:
+    # the mixed path stays within a stated distance of the FP64 path after 60 steps
+    n = 256
+    x, dx = inputs.axis(n, -1.0, 1.0, "linextrap")
+    phi0 = inputs.phi0_riemann_2d(x, x)
+    out = {}
+    for prec in ("fp64", "mixed"):
+        case = Case(2, n, n, "sin2d", bc="linextrap", precision=prec)
+        with case.solver() as s:
+            s.set_phi0(phi0)
+            s.advance(60)
+            s.sync()
+            out[prec] = s.get_phi()
+    assert np.all(np.isfinite(out["mixed"]))
+    assert np.max(np.abs(out["mixed"] - out["fp64"])) < 1e-4
+
+
+def test_gpu_reproduces_table3_orders():
+    # FP64 GPU solve of Example 3 with dt ~ dx^{5/3}: errors within 2x of Table 3 at 40^2 and 80^2
+    import exact
+
+    tf = 0.5 / math.pi**2
+    res = {}
+    for n in (40, 80):
+        x, dx = inputs.axis(n, -2.0, 2.0, "periodic")
+        case = Case(2, n, n, "burgers2d", lo=-2.0, hi=2.0, dt_mode="dx53")
+        with case.solver() as s:
+            s.set_phi0(inputs.phi0_negcos_diag_2d(x, x))
+            s.step_to(tf)
+            e = np.abs(s.get_phi() - exact.negcos_diag_2d("burgers2d", x, x, tf))
+        res[n] = e.max()
+    assert 1.43e-4 / 2 < res[40] < 1.43e-4 * 2
+    assert 6.34e-6 / 2 < res[80] < 6.34e-6 * 2
