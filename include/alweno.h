@@ -199,6 +199,45 @@ alw_status alw_set_state(alw_solver *s, const alw_state *state, const double *ho
 alw_status alw_memory_bytes(alw_solver *s, size_t *bytes);
 
 /* ------------------------------------------------------------------------
+ * Batches: many independent 2D periodic instances of uneven size (grids,
+ * Hamiltonians, phase-shifted initial data and end times may all differ)
+ * advanced together by one persistent launch per RK stage over a shared
+ * work list of (instance, tile) pairs, replayed from a CUDA graph until every
+ * instance has reached its own t_final.  Each instance follows exactly the
+ * same arithmetic as a single solver with the same scheme (same dt rule,
+ * alpha, weights), so its result does not depend on the other instances.
+ * Precision must be FP32 or MIXED; alpha_mode DEFAULT, GLOBAL_LAGGED,
+ * LOCAL_LAGGED or FIXED.  Not a construct of the paper: it serves many solves
+ * per device. */
+typedef struct alw_batch alw_batch;
+
+/* Work-list orders the autotuner chooses from. */
+enum { ALW_ORDER_INSTANCE = 0, ALW_ORDER_LARGEST_FIRST = 1, ALW_ORDER_INTERLEAVED = 2 };
+
+typedef struct {
+  int32_t order;            /* ALW_ORDER_* */
+  int32_t steps_per_graph;  /* RK3 steps captured per graph replay (1..256) */
+  int32_t grid_ctas;        /* persistent CTAs; 0 = as many as fit on the device */
+} alw_batch_tuning;
+
+alw_status alw_batch_create(const alw_scheme *scheme, void *cuda_stream, alw_batch **out);
+/* Add an instance (grid dim 2, periodic; host_phi0 of n = nx*ny doubles, copied).
+ * id_out receives its index.  ALW_EBUSY after the batch has run. */
+alw_status alw_batch_add(alw_batch *b, const alw_grid *grid, const alw_hamiltonian *ham, const double *host_phi0,
+                         size_t n, double t_final, int32_t *id_out);
+/* Fix the tuning (NULL: let the autotuner choose on the next run). */
+alw_status alw_batch_set_tuning(alw_batch *b, const alw_batch_tuning *tuning);
+alw_status alw_batch_get_tuning(alw_batch *b, alw_batch_tuning *tuning);
+/* Advance every instance to its t_final; returns after all have arrived.
+ * replays_out (nullable): graph replays used.  ALW_ENONFINITE if an instance
+ * saw a non-finite dH/dp (the others still finish). */
+alw_status alw_batch_run(alw_batch *b, int64_t *replays_out);
+alw_status alw_batch_get_phi(alw_batch *b, int32_t id, double *host_out, size_t n);
+alw_status alw_batch_get_state(alw_batch *b, int32_t id, alw_state *state);
+alw_status alw_batch_memory_bytes(alw_batch *b, size_t *bytes);
+alw_status alw_batch_destroy(alw_batch *b);
+
+/* ------------------------------------------------------------------------
  * No-allocation entry point (the paper has no counterpart; it serves callers
  * that cannot obtain device memory on demand, e.g. a framework whose pool
  * allocator owns all device memory, or a real-time loop that must not

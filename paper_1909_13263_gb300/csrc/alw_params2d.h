@@ -6,17 +6,46 @@
 
 namespace alw {
 
-struct alignas(64) Stage2DParams {
+// One problem instance inside the shared padded arrays.  A single solver has
+// one instance at row offset 0; a batch stacks many instances vertically in
+// arrays of one common pitch, each in its own block of rows.
+struct InstDesc {
+  int nx, ny;            // interior nodes
+  int tiles_x, tiles_y;  // tile grid of this instance
+  int row_off;           // padded row of this instance's first (ghost) row
+  int ham, bc;           // Hamiltonian kind, boundary condition
+  int ntiles;            // tiles_x * tiles_y
+  float dx, dy, rdx, rdy;
+  double lx, ly;         // dt = cfl / (ax/lx + ay/ly)
+  DevState *st;          // this instance's device-side time and alpha state
+};
+
+struct Stage2DParams {
   CUtensorMap maps[6];  // FP32: 0 = phi^n, 1 = stage-1 state, 2 = stage-2 state;
                         // MIXED: 0/1 = hi pairs, 2/3 = lo pairs, 4 = delta_1, 5 = delta_2
-  StageParams p;
+  StageParams p;        // stage, modes, slots, pitch and buffers (per-instance fields unused in a batch)
   int map_a, map_b, map_c;  // FP32: source, base (-1: none); MIXED: hi base index, lo base index, delta (-1: none)
+  int ntiles;               // work-list length
+  const InstDesc *insts;    // batch: instance table (nullptr: the single instance `inst0`)
+  const int *tiles;         // batch: work list, entry = instance * 65536 + tile of that instance
+  int *done_count;          // batch: incremented when an instance reaches its t_final (may be null)
+  InstDesc inst0;
 };
 
 // TMA box of one tile with its halo (floats): 72 columns x 38 rows.
 constexpr int kBox2DW = 72, kBox2DH = 38;
+constexpr int kTile2DX = 64, kTile2DY = 32;
 
 int launch_stage2d_f32(const Stage2DParams &prm, void *stream);
 int launch_stage2d_mixed(const Stage2DParams &prm, void *stream);
+// occupancy-limited CTA count of the persistent kernel (for work-list sizing)
+int stage2d_grid_cap_f32(int weights);
+int stage2d_grid_cap_mixed(int weights);
+
+// Host helpers shared by the solver and batch runtimes (alw_runtime.cu).
+void *dev_alloc(size_t bytes, void *stream);
+void dev_free(void *ptr, size_t bytes, void *stream);
+// 2D float tensor map over a padded array of `pitch` x `rows` floats, box = one tile plus halo; 0 on success
+int encode_tile_map(CUtensorMap *map, void *base, long long pitch, long long rows);
 
 }  // namespace alw

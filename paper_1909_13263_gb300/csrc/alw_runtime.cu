@@ -48,7 +48,7 @@ alw_status fail(alw_status st, const char *fmt, ...) {
 std::mutex g_alloc_mu;
 alw_allocator g_alloc = {nullptr, nullptr, nullptr};
 
-void *dev_alloc(size_t bytes, cudaStream_t s) {
+void *dev_alloc_impl(size_t bytes, cudaStream_t s) {
   alw_allocator a;
   {
     std::lock_guard<std::mutex> lk(g_alloc_mu);
@@ -63,7 +63,7 @@ void *dev_alloc(size_t bytes, cudaStream_t s) {
   return p;
 }
 
-void dev_free(void *p, size_t bytes, cudaStream_t s) {
+void dev_free_impl(void *p, size_t bytes, cudaStream_t s) {
   if (!p) return;
   alw_allocator a;
   {
@@ -77,6 +77,39 @@ void dev_free(void *p, size_t bytes, cudaStream_t s) {
 }  // namespace
 
 void alw::set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+
+int alw::encode_tile_map(CUtensorMap *m, void *base, long long pitch, long long rows) {
+  auto enc = tensor_map_encoder_fn();
+  if (!enc) return -1;
+  const cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)kBox2DW, (cuuint32_t)kBox2DH};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : (int)r;
+}
+
+void *alw::dev_alloc(size_t bytes, void *stream) { return dev_alloc_impl(bytes, reinterpret_cast<cudaStream_t>(stream)); }
+void alw::dev_free(void *ptr, size_t bytes, void *stream) {
+  dev_free_impl(ptr, bytes, reinterpret_cast<cudaStream_t>(stream));
+}
 
 int alw::tile_x(int prec, int dim) {
   if (dim == 1) return TX1D;
@@ -113,7 +146,7 @@ struct alw_solver {
   CUtensorMap maps[6];      // tensor maps of the padded arrays (see Stage2DParams)
 
   void *alloc(size_t bytes) {
-    void *p = dev_alloc(bytes, stream);
+    void *p = dev_alloc_impl(bytes, stream);
     if (p) allocs.emplace_back(p, bytes);
     return p;
   }
@@ -130,8 +163,29 @@ int kernel_prec(int precision) {
 int launch_stage(const alw_solver *s, const StageParams &p) {
   if (s->use2d) {
     Stage2DParams q;
+    memset(&q, 0, sizeof q);
     memcpy(q.maps, s->maps, sizeof q.maps);
     q.p = p;
+    q.ntiles = s->tiles_x * s->tiles_y;
+    q.insts = nullptr;
+    q.tiles = nullptr;
+    q.done_count = nullptr;
+    InstDesc &d = q.inst0;
+    d.nx = s->nx;
+    d.ny = s->ny;
+    d.tiles_x = s->tiles_x;
+    d.tiles_y = s->tiles_y;
+    d.row_off = 0;
+    d.ham = s->ham.kind;
+    d.bc = s->grid.bc;
+    d.ntiles = q.ntiles;
+    d.dx = (float)s->dx;
+    d.dy = (float)s->dy;
+    d.rdx = (float)(1.0 / s->dx);
+    d.rdy = (float)(1.0 / s->dy);
+    d.lx = s->lx;
+    d.ly = s->ly;
+    d.st = s->st;
     const int which = p.stage == 0 ? p.src_of : p.stage;
     if (s->prec == P_MIXED) {
       q.map_a = 0;
@@ -281,7 +335,7 @@ alw_status load_phi_dense(alw_solver *s, const void *dense, int dtype) {
     const double *src = (const double *)dense;
     void *tmp = nullptr;
     if (dtype != 0) {  // widen floats to doubles first
-      tmp = dev_alloc((size_t)s->nx * s->ny * sizeof(double), s->stream);
+      tmp = dev_alloc_impl((size_t)s->nx * s->ny * sizeof(double), s->stream);
       if (!tmp) return fail(ALW_ENOMEM, "device allocation of %zu bytes failed", (size_t)s->nx * s->ny * 8);
       // dense float -> dense double through the pack path is not available; use unpack into H[1] scratch-free:
       // convert elementwise with a padded round trip via H[1] as float and a join of (H[1], 0)
@@ -291,7 +345,7 @@ alw_status load_phi_dense(alw_solver *s, const void *dense, int dtype) {
       src = (const double *)tmp;
     }
     ALW_LAUNCH(launch_mixed_split(src, s->H[0], s->Lo[0], s->nx, s->ny, s->pitch, s->dim, s->stream));
-    if (tmp) dev_free(tmp, (size_t)s->nx * s->ny * sizeof(double), s->stream);
+    if (tmp) dev_free_impl(tmp, (size_t)s->nx * s->ny * sizeof(double), s->stream);
   } else {
     ALW_LAUNCH(launch_unpack(dense, dtype, s->P, s->prec == P_F64 ? 0 : 1, s->nx, s->ny, s->pitch, s->dim, s->stream));
   }
@@ -325,32 +379,12 @@ alw_status prime_alpha(alw_solver *s) {
   return ALW_OK;
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void *ptr = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
-    cudaGetLastError();
-  }
-  return fn;
-}
 
 // 2D float tensor map over a padded array: box = one tile plus halo.
 alw_status make_tensor_map(alw_solver *s, CUtensorMap *m, void *base) {
-  auto enc = tensor_map_encoder();
-  if (!enc) return fail(ALW_ECUDA, "cuTensorMapEncodeTiled is not available");
-  const cuuint64_t dims[2] = {(cuuint64_t)s->pitch, (cuuint64_t)s->rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)s->pitch * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)kBox2DW, (cuuint32_t)kBox2DH};
-  const cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return fail(ALW_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  const int r = encode_tile_map(m, base, s->pitch, s->rows);
+  if (r == -1) return fail(ALW_ECUDA, "cuTensorMapEncodeTiled is not available");
+  if (r != 0) return fail(ALW_ECUDA, "cuTensorMapEncodeTiled failed (%d)", r);
   return ALW_OK;
 }
 
@@ -487,7 +521,7 @@ alw_status alw_destroy(alw_solver *s) {
   cudaStreamSynchronize(s->stream);
   if (s->g_step) cudaGraphExecDestroy(s->g_step);
   if (s->g_adv) cudaGraphExecDestroy(s->g_adv);
-  for (auto &a : s->allocs) dev_free(a.first, a.second, s->stream);
+  for (auto &a : s->allocs) dev_free_impl(a.first, a.second, s->stream);
   cudaStreamSynchronize(s->stream);
   if (s->h_st) cudaFreeHost(s->h_st);
   if (s->h_tf) cudaFreeHost(s->h_tf);
@@ -523,11 +557,11 @@ alw_status alw_set_phi0_device(alw_solver *s, const void *dev_phi, int32_t dtype
 alw_status alw_set_phi0(alw_solver *s, const double *host_phi, size_t n) {
   if (!s || !host_phi) return fail(ALW_EINVAL, "NULL argument");
   if (n != (size_t)s->nx * s->ny) return fail(ALW_EINVAL, "n = %zu but nx*ny = %zu", n, (size_t)s->nx * s->ny);
-  void *tmp = dev_alloc(n * sizeof(double), s->stream);
+  void *tmp = dev_alloc_impl(n * sizeof(double), s->stream);
   if (!tmp) return fail(ALW_ENOMEM, "device allocation of %zu bytes failed", n * sizeof(double));
   cudaError_t e = cudaMemcpyAsync(tmp, host_phi, n * sizeof(double), cudaMemcpyHostToDevice, s->stream);
   alw_status st = e == cudaSuccess ? alw_set_phi0_device(s, tmp, 0, n) : fail(ALW_ECUDA, "copy: %s", cudaGetErrorString(e));
-  dev_free(tmp, n * sizeof(double), s->stream);
+  dev_free_impl(tmp, n * sizeof(double), s->stream);
   if (st == ALW_OK) ALW_CUDA(cudaStreamSynchronize(s->stream));
   return st;
 }
@@ -624,17 +658,17 @@ static alw_status gather_dense(alw_solver *s, int which, void *dst, int dtype) {
     if (dtype == 0) {
       ALW_LAUNCH(launch_mixed_join(s->H[cur], s->Lo[cur], delta, (double *)dst, s->nx, s->ny, s->pitch, s->dim, s->stream));
     } else {
-      void *tmp = dev_alloc(n * sizeof(double), s->stream);
+      void *tmp = dev_alloc_impl(n * sizeof(double), s->stream);
       if (!tmp) return fail(ALW_ENOMEM, "device allocation failed");
       ALW_LAUNCH(launch_mixed_join(s->H[cur], s->Lo[cur], delta, (double *)tmp, s->nx, s->ny, s->pitch, s->dim, s->stream));
       // narrow doubles to floats via the padded float array H[cur^1] used as a scratch-free converter is unsafe;
       // convert directly with the unpack/pack pair on a temporary padded buffer
-      void *pad = dev_alloc(s->arr_bytes, s->stream);
+      void *pad = dev_alloc_impl(s->arr_bytes, s->stream);
       if (!pad) return fail(ALW_ENOMEM, "device allocation failed");
       ALW_LAUNCH(launch_unpack(tmp, 0, pad, 1, s->nx, s->ny, s->pitch, s->dim, s->stream));
       ALW_LAUNCH(launch_pack(pad, 1, dst, 1, s->nx, s->ny, s->pitch, s->dim, s->stream));
-      dev_free(pad, s->arr_bytes, s->stream);
-      dev_free(tmp, n * sizeof(double), s->stream);
+      dev_free_impl(pad, s->arr_bytes, s->stream);
+      dev_free_impl(tmp, n * sizeof(double), s->stream);
     }
   } else {
     const void *src = which == 1 ? s->A : (which == 2 ? s->B : s->P);
@@ -657,14 +691,14 @@ static alw_status get_host(alw_solver *s, int which, double *host_out, size_t n)
   if (st) return st;
   if (!host_out) return fail(ALW_EINVAL, "NULL output");
   if (n != (size_t)s->nx * s->ny) return fail(ALW_EINVAL, "n = %zu but nx*ny = %zu", n, (size_t)s->nx * s->ny);
-  void *tmp = dev_alloc(n * sizeof(double), s->stream);
+  void *tmp = dev_alloc_impl(n * sizeof(double), s->stream);
   if (!tmp) return fail(ALW_ENOMEM, "device allocation failed");
   st = gather_dense(s, which, tmp, 0);
   if (st == ALW_OK) {
     cudaError_t e = cudaMemcpyAsync(host_out, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
     if (e != cudaSuccess) st = fail(ALW_ECUDA, "copy: %s", cudaGetErrorString(e));
   }
-  dev_free(tmp, n * sizeof(double), s->stream);
+  dev_free_impl(tmp, n * sizeof(double), s->stream);
   ALW_CUDA(cudaStreamSynchronize(s->stream));
   return st;
 }
@@ -695,11 +729,11 @@ alw_status alw_get_state(alw_solver *s, alw_state *state) {
 alw_status alw_set_state(alw_solver *s, const alw_state *state, const double *host_phi, size_t n) {
   if (!s || !state || !host_phi) return fail(ALW_EINVAL, "NULL argument");
   if (n != (size_t)s->nx * s->ny) return fail(ALW_EINVAL, "n = %zu but nx*ny = %zu", n, (size_t)s->nx * s->ny);
-  void *tmp = dev_alloc(n * sizeof(double), s->stream);
+  void *tmp = dev_alloc_impl(n * sizeof(double), s->stream);
   if (!tmp) return fail(ALW_ENOMEM, "device allocation failed");
   ALW_CUDA(cudaMemcpyAsync(tmp, host_phi, n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
   alw_status st = load_phi_dense(s, tmp, 0);
-  dev_free(tmp, n * sizeof(double), s->stream);
+  dev_free_impl(tmp, n * sizeof(double), s->stream);
   if (st) return st;
   st = reset_state(s, state->t, state->steps, state->alpha);
   if (st) return st;

@@ -1,9 +1,12 @@
-// Persistent 2D stage kernel for float arithmetic (FP32 and MIXED) on sm_103a.
+// Persistent 2D stage kernel for float arithmetic (FP32 and MIXED) on sm_103a,
+// for one instance or a batch of instances stacked in shared padded arrays.
 //
-// Each CTA walks tiles tile = blockIdx.x + k * gridDim.x.  The raw arrays of
-// the next tile (phi or hi/lo/delta, with a 3-node halo; one TMA box per
-// array) are loaded into the other half of a double buffer while the current
-// tile is computed.  Per tile:
+// Each CTA walks the work list (tile = blockIdx.x + k * gridDim.x).  Thread 0
+// prepares the next tile -- decodes its instance, decides whether the instance
+// still needs work, computes the instance's dt and flux alpha for this stage,
+// and issues one TMA box per array (tile plus 3-node halo) into the other half
+// of a double buffer on an mbarrier -- while all threads compute the current
+// tile:
 //   1. differences pass: Delta^+ phi along x (dX) and y (dY) for every cell,
 //      combining the MIXED parts (hi + lo + delta) once per cell;
 //   2. x sweep: warp w takes nodes 8w..8w+7 of every row (one row per lane;
@@ -11,8 +14,9 @@
 //      writes phi_x^-/+ to shared memory;
 //   3. y sweep: each lane takes 8 consecutive nodes of one column, forms the
 //      Lax-Friedrichs Hamiltonian and the RK combination, and stores.
-// The same sweep code serves both directions.  Alpha is folded into a
-// per-thread maximum and reduced once per CTA at the end.
+// After each tile the CTA folds max |dH/dp|, |dH/dq| into the instance's slot;
+// the CTA that completes an instance's last tile closes the instance's stage
+// (dt, time, step count, buffer flip), so instances advance independently.
 #pragma once
 #include "alw_device.cuh"
 #include "alw_params2d.h"
@@ -60,8 +64,36 @@ template <> struct Ham2<H_EIKONAL2D> {
   }
 };
 
+// Compile-time kind H >= 0, or H = -1: the kind is read per instance (batches mixing Hamiltonians).
+template <int H> struct HamSel {
+  int kind;
+  __device__ __forceinline__ float value(float p, float q) const { return Ham2<H>::value(p, q); }
+  __device__ __forceinline__ void alpha(float um, float up, float vm, float vp, float &ax, float &ay) const {
+    Ham2<H>::alpha(um, up, vm, vp, ax, ay);
+  }
+};
+template <> struct HamSel<-1> {
+  int kind;
+  __device__ __forceinline__ float value(float p, float q) const {
+    switch (kind) {
+      case H_NEGCOS2D: return Ham2<H_NEGCOS2D>::value(p, q);
+      case H_SIN2D: return Ham2<H_SIN2D>::value(p, q);
+      case H_EIKONAL2D: return Ham2<H_EIKONAL2D>::value(p, q);
+      default: return Ham2<H_BURGERS2D>::value(p, q);
+    }
+  }
+  __device__ __forceinline__ void alpha(float um, float up, float vm, float vp, float &ax, float &ay) const {
+    switch (kind) {
+      case H_NEGCOS2D: Ham2<H_NEGCOS2D>::alpha(um, up, vm, vp, ax, ay); break;
+      case H_SIN2D: Ham2<H_SIN2D>::alpha(um, up, vm, vp, ax, ay); break;
+      case H_EIKONAL2D: Ham2<H_EIKONAL2D>::alpha(um, up, vm, vp, ax, ay); break;
+      default: Ham2<H_BURGERS2D>::alpha(um, up, vm, vp, ax, ay);
+    }
+  }
+};
+
 struct Geo2D {
-  static constexpr int TX = 64, TY = 32, K = 8, NT = 256;
+  static constexpr int TX = kTile2DX, TY = kTile2DY, K = 8, NT = 256;
   static constexpr int SW = TX + 8, SH = TY + 6;        // TMA box (halo 4 columns / 3 rows each side)
   static constexpr int ARR = ((SH * SW + 31) / 32) * 32; // floats per array slot (128-byte multiple)
   static constexpr int DXW = TX + 5, DXP = 73;          // x differences: width, odd pitch
@@ -71,6 +103,14 @@ struct Geo2D {
     return 128 + sizeof(float) * (size_t)(2 * NARR * ARR + TY * DXP + DYH * TX) + sizeof(float2) * (size_t)TY * SUP;
   }
 };
+static_assert(Geo2D::SW == kBox2DW && Geo2D::SH == kBox2DH, "TMA box must match the tile halo");
+
+// Per-tile values prepared by thread 0 when the tile's loads are issued.
+struct TileInfo {
+  int inst, tx0, ty0, cur, skip, last;
+  float dtf, fax, fay;
+  double dt;
+};
 
 template <int PREC, int W, int H>
 __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_constant__ Stage2DParams prm) {
@@ -79,42 +119,48 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
   constexpr int DXW = Geo2D::DXW, DXP = Geo2D::DXP, DYH = Geo2D::DYH, SUP = Geo2D::SUP;
   constexpr int NARR = (PREC == P_MIXED) ? 3 : 2;
   const StageParams &p = prm.p;
-  DevState *st = p.state;
-  if (p.loop_mode == LOOP_STEP_TO && !(st->t < st->t_final)) return;
-  if (st->err) return;
+  const bool batch = prm.insts != nullptr;
+  if (!batch) {
+    const DevState *st = prm.inst0.st;
+    if (p.loop_mode == LOOP_STEP_TO && !(st->t < st->t_final)) return;
+    if (st->err) return;
+  }
 
   extern __shared__ __align__(128) unsigned char smem_dyn[];
   // TMA destinations are kept 128-byte aligned (the launch adds 128 bytes of slack)
   unsigned char *smem = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
-  float *raw = reinterpret_cast<float *>(smem);          // [2][NARR][ARR]
-  float *dX = raw + 2 * NARR * ARR;                      // [TY][DXP]
-  float *dY = dX + TY * DXP;                             // [DYH][TX]
+  float *raw = reinterpret_cast<float *>(smem);            // [2][NARR][ARR]
+  float *dX = raw + 2 * NARR * ARR;                        // [TY][DXP]
+  float *dY = dX + TY * DXP;                               // [DYH][TX]
   float2 *su = reinterpret_cast<float2 *>(dY + DYH * TX);  // [TY][SUP] (offset is an even float count)
   __shared__ __align__(8) uint64_t bars[2];
+  __shared__ TileInfo s_info[2];
   __shared__ float s_red[2][NT / 32];
-  __shared__ double s_dt;
-  __shared__ int s_lastflag, s_last;
-  __shared__ float s_fax, s_fay, s_dtf;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int tiles = p.tiles_x * p.tiles_y;
-  const int cur = (PREC == P_MIXED) ? st->cur : 0;
+  const int ntiles = prm.ntiles;
   const bool local_alpha = (p.alpha_mode == A_LOCAL_LAGGED || p.alpha_mode == A_LOCAL_EXACT);
+  const float eps = (float)p.eps;
+  const uint32_t box_bytes = (uint32_t)(SH * SW * sizeof(float));
 
-  // tensor maps of this stage
-  const CUtensorMap *mA, *mB = nullptr, *mC = nullptr;
-  if (PREC == P_MIXED) {
-    mA = &prm.maps[prm.map_a + cur];
-    mB = &prm.maps[prm.map_b + cur];
-    if (prm.map_c >= 0) mC = &prm.maps[prm.map_c];
-  } else {
-    mA = &prm.maps[prm.map_a];
-    if (prm.map_b >= 0) mB = &prm.maps[prm.map_b];
-  }
-  const int nmaps = 1 + (mB != nullptr) + (mC != nullptr);
-  const bool has_delta = (mC != nullptr);
+  auto desc = [&](int inst) -> const InstDesc & { return batch ? prm.insts[inst] : prm.inst0; };
 
-  if (tid == 0) {
+  // thread 0: decode work-list entry t, compute its instance's stage scalars, issue its loads into buffer b
+  auto prepare = [&](int t, int b) {
+    int inst = 0, tl = t;
+    if (batch) {
+      const int e = prm.tiles[t];
+      inst = e >> 16;
+      tl = e & 0xffff;
+    }
+    const InstDesc &d = desc(inst);
+    const DevState *st = d.st;
+    TileInfo info;
+    info.inst = inst;
+    info.tx0 = (tl % d.tiles_x) * TX;
+    info.ty0 = (tl / d.tiles_x) * TY;
+    info.cur = (PREC == P_MIXED) ? st->cur : 0;
+    info.skip = (st->err != 0) || (p.loop_mode == LOOP_STEP_TO && !(st->t < st->t_final));
     double dt;
     int last = 0;
     if (p.stage == 1 && p.loop_mode != LOOP_STAGE) {
@@ -126,7 +172,7 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
         ax = bits_to_double(st->alpha_bits[p.dt_slot][0]);
         ay = bits_to_double(st->alpha_bits[p.dt_slot][1]);
       }
-      const double den = ax / p.lx + ay / p.ly;
+      const double den = ax / d.lx + ay / d.ly;
       dt = den > 0.0 ? p.cfl / den : (p.loop_mode == LOOP_ADVANCE ? 0.0 : INFINITY);
       if (p.loop_mode == LOOP_STEP_TO && st->t + dt >= st->t_final) {
         dt = st->t_final - st->t;
@@ -137,9 +183,9 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
     } else {
       dt = st->dt;
     }
-    s_dt = dt;
-    s_dtf = (float)dt;
-    s_lastflag = last;
+    info.dt = dt;
+    info.dtf = (float)dt;
+    info.last = last;
     float fax = 0.0f, fay = 0.0f;
     if (p.alpha_mode == A_FIXED) {
       fax = (float)p.alpha_fixed[0];
@@ -148,53 +194,71 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
       fax = (float)bits_to_double(st->alpha_bits[p.read_slot][0]);
       fay = (float)bits_to_double(st->alpha_bits[p.read_slot][1]);
     }
-    s_fax = fax;
-    s_fay = fay;
+    info.fax = fax;
+    info.fay = fay;
+    s_info[b] = info;
+    if (info.skip) return;
+    const CUtensorMap *mA, *mB = nullptr, *mC = nullptr;
+    if (PREC == P_MIXED) {
+      mA = &prm.maps[prm.map_a + info.cur];
+      mB = &prm.maps[prm.map_b + info.cur];
+      if (prm.map_c >= 0) mC = &prm.maps[prm.map_c];
+    } else {
+      mA = &prm.maps[prm.map_a];
+      if (prm.map_b >= 0) mB = &prm.maps[prm.map_b];
+    }
+    const int nm = 1 + (mB != nullptr) + (mC != nullptr);
+    float *dst = raw + b * NARR * ARR;
+    const int y = d.row_off + info.ty0;
+    mbar_arrive_expect_tx(&bars[b], box_bytes * nm);
+    tma_load_2d(dst, mA, info.tx0, y, &bars[b]);
+    if (mB) tma_load_2d(dst + ARR, mB, info.tx0, y, &bars[b]);
+    if (mC) tma_load_2d(dst + 2 * ARR, mC, info.tx0, y, &bars[b]);
+  };
+
+  if (tid == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
     fence_mbar_init();
+    if ((int)blockIdx.x < ntiles) prepare(blockIdx.x, 0);
   }
   __syncthreads();
-  const float dtf = s_dtf, fax = s_fax, fay = s_fay;
 
-  const uint32_t box_bytes = (uint32_t)(SH * SW * sizeof(float));
-  auto issue = [&](int tile, int buf) {
-    const int tx0 = (tile % p.tiles_x) * TX, ty0 = (tile / p.tiles_x) * TY;
-    float *dst = raw + buf * NARR * ARR;
-    mbar_arrive_expect_tx(&bars[buf], box_bytes * nmaps);
-    tma_load_2d(dst, mA, tx0, ty0, &bars[buf]);
-    if (mB) tma_load_2d(dst + ARR, mB, tx0, ty0, &bars[buf]);
-    if (mC) tma_load_2d(dst + 2 * ARR, mC, tx0, ty0, &bars[buf]);
-  };
-
-  const float dx = (float)p.dx, dy = (float)p.dy, rdx = (float)p.rdx, rdy = (float)p.rdy, eps = (float)p.eps;
-  float amx = 0.0f, amy = 0.0f;
-  bool bad = false;
+  uint32_t phase = 0;  // bit b: parity of the next completion of bars[b]
   int k = 0;
-  int tile = blockIdx.x;
-  if (tid == 0 && tile < tiles) issue(tile, 0);
-
-  for (; tile < tiles; tile += gridDim.x, ++k) {
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
     const int buf = k & 1;
-    const int next = tile + gridDim.x;
-    if (tid == 0 && next < tiles) {
+    const int next = t + gridDim.x;
+    if (tid == 0 && next < ntiles) {
       fence_proxy_async_smem();
-      issue(next, buf ^ 1);
+      prepare(next, buf ^ 1);
     }
-    const bool ok = mbar_wait_bounded(&bars[buf], (uint32_t)((k >> 1) & 1));
+    const TileInfo info = s_info[buf];
+    if (info.skip) {
+      __syncthreads();
+      continue;
+    }
+    const bool ok = mbar_wait_bounded(&bars[buf], (phase >> buf) & 1u);
     if (__syncthreads_or(!ok)) {
-      // a tile load never completed: flag it, let the other in-flight load land, stop
+      // a tile load never completed: flag the instance, let the other in-flight load land, stop
       if (tid == 0) {
-        atomicOr(&st->err, 2);
-        if (next < tiles) mbar_wait_bounded(&bars[buf ^ 1], (uint32_t)(((k + 1) >> 1) & 1));
+        atomicOr(&desc(info.inst).st->err, 2);
+        if (next < ntiles && !s_info[buf ^ 1].skip) mbar_wait_bounded(&bars[buf ^ 1], (phase >> (buf ^ 1)) & 1u);
       }
       __syncthreads();
       return;
     }
-    const int tx0 = (tile % p.tiles_x) * TX, ty0 = (tile / p.tiles_x) * TY;
+    phase ^= 1u << buf;
+
+    const InstDesc &d = desc(info.inst);
+    const int nx = d.nx, ny = d.ny, tx0 = info.tx0, ty0 = info.ty0;
+    const size_t rbase = (size_t)d.row_off * p.pitch;   // element offset of the instance's rows
+    const HamSel<H> ham{d.ham};
+    const float dtf = info.dtf, fax = info.fax, fay = info.fay;
     const float *A = raw + buf * NARR * ARR;
     const float *B = A + ARR;
     const float *C = A + 2 * ARR;
+    const bool has_delta = PREC == P_MIXED && prm.map_c >= 0;
 
     // ---- 1. differences (rows by warp, columns by lane: no division, conflict-free)
     auto cell_diff = [&](int i0, int i1) -> float {
@@ -208,20 +272,22 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
 #pragma unroll
       for (int c = lane; c < DXW; c += 32) {
         const int i0 = (r + 3) * SW + c + 1;
-        dX[r * DXP + c] = cell_diff(i0, i0 + 1) * rdx;
+        dX[r * DXP + c] = cell_diff(i0, i0 + 1) * d.rdx;
       }
     }
     for (int r = warp; r < DYH; r += NT / 32) {
 #pragma unroll
       for (int c = lane; c < TX; c += 32) {
         const int i0 = r * SW + c + 4;
-        dY[r * TX + c] = cell_diff(i0, i0 + SW) * rdy;
+        dY[r * TX + c] = cell_diff(i0, i0 + SW) * d.rdy;
       }
     }
     __syncthreads();
 
-    const bool edge = (tx0 < 3) || (tx0 + TX > p.nx - 3) || (ty0 < 3) || (ty0 + TY > p.ny - 3);
+    const bool edge = (tx0 < 3) || (tx0 + TX > nx - 3) || (ty0 < 3) || (ty0 + TY > ny - 3);
     const int colY = ((warp & 1) << 5) + lane, segY = warp >> 1;
+    float amx = 0.0f, amy = 0.0f;
+    bool bad = false;
 
     // ---- 2./3. sweeps (one code path for both directions)
 #pragma unroll 1
@@ -237,10 +303,10 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
         // node (colY, y) of the tile: phi_y^-/+ = (dmq, dpq)
         const int y = K * segY + q;
         const int gi = tx0 + colY, gj = ty0 + y;
-        const bool inside = !edge || (gi < p.nx && gj < p.ny);
+        const bool inside = !edge || (gi < nx && gj < ny);
         const float2 u = su[y * SUP + colY];
         float ax, ay;
-        Ham2<H>::alpha(u.x, u.y, dmq, dpq, ax, ay);
+        ham.alpha(u.x, u.y, dmq, dpq, ax, ay);
         if (inside) {
           if (!isfinite(u.x + u.y + dmq + dpq)) bad = true;
           amx = fmaxf(amx, ax);
@@ -248,29 +314,29 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
         }
         if (p.stage == 0 || !inside) return;
         const float aX = local_alpha ? ax : fax, aY = local_alpha ? ay : fay;
-        const float Hv = Ham2<H>::value(0.5f * (u.y + u.x), 0.5f * (dpq + dmq));
+        const float Hv = ham.value(0.5f * (u.y + u.x), 0.5f * (dpq + dmq));
         const float L = fmaf(aX * 0.5f, u.y - u.x, fmaf(aY * 0.5f, dpq - dmq, -Hv));
         const int sidx = (y + 3) * SW + colY + 4;
-        const size_t g = (size_t)(gj + GY) * p.pitch + gi + GX;
+        const size_t g = rbase + (size_t)(gj + GY) * p.pitch + gi + GX;
         if (PREC == P_MIXED) {
           if (p.stage == 3) {
-            const float d = (2.0f / 3.0f) * fmaf(dtf, L, C[sidx]);
+            const float dd = (2.0f / 3.0f) * fmaf(dtf, L, C[sidx]);
             float h, l;
-            df_add(A[sidx], B[sidx], d, h, l);
-            float *oh = reinterpret_cast<float *>(p.mix_hi[cur ^ 1]);
-            float *ol = reinterpret_cast<float *>(p.mix_lo[cur ^ 1]);
+            df_add(A[sidx], B[sidx], dd, h, l);
+            float *oh = reinterpret_cast<float *>(p.mix_hi[info.cur ^ 1]);
+            float *ol = reinterpret_cast<float *>(p.mix_lo[info.cur ^ 1]);
             if (edge) {
-              store_node<float, 2>(oh, p.pitch, p.nx, p.ny, p.bc, gi, gj, h);
-              store_node<float, 2>(ol, p.pitch, p.nx, p.ny, p.bc, gi, gj, l);
+              store_node<float, 2>(oh + rbase, p.pitch, nx, ny, d.bc, gi, gj, h);
+              store_node<float, 2>(ol + rbase, p.pitch, nx, ny, d.bc, gi, gj, l);
             } else {
               oh[g] = h;
               ol[g] = l;
             }
           } else {
-            const float d = (p.stage == 1) ? dtf * L : 0.25f * fmaf(dtf, L, C[sidx]);
+            const float dd = (p.stage == 1) ? dtf * L : 0.25f * fmaf(dtf, L, C[sidx]);
             float *o = reinterpret_cast<float *>(p.out0);
-            if (edge) store_node<float, 2>(o, p.pitch, p.nx, p.ny, p.bc, gi, gj, d);
-            else o[g] = d;
+            if (edge) store_node<float, 2>(o + rbase, p.pitch, nx, ny, d.bc, gi, gj, dd);
+            else o[g] = dd;
           }
         } else {
           const float src = A[sidx];
@@ -283,61 +349,63 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
             outv = fmaf(1.0f / 3.0f, B[sidx], (2.0f / 3.0f) * fmaf(dtf, L, src));
           }
           float *o = reinterpret_cast<float *>(p.out0);
-          if (edge) store_node<float, 2>(o, p.pitch, p.nx, p.ny, p.bc, gi, gj, outv);
+          if (edge) store_node<float, 2>(o + rbase, p.pitch, nx, ny, d.bc, gi, gj, outv);
           else o[g] = outv;
         }
       };
-      sweep_stream<K, W>(v_at, dir == 0 ? rdx : rdy, 0.5f * (dir == 0 ? dx : dy), eps, emit);
+      sweep_stream<K, W>(v_at, dir == 0 ? d.rdx : d.rdy, 0.5f * (dir == 0 ? d.dx : d.dy), eps, emit);
       if (dir == 0) __syncthreads();
     }
-    __syncthreads();  // raw[buf], dX, dY, su are free for the next tile
-  }
 
-  // ---- grid maximum of alpha: one atomic per CTA
+    // ---- this tile's maximum of alpha into the instance's slot; close the instance's stage
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    amx = fmaxf(amx, __shfl_xor_sync(0xffffffffu, amx, o));
-    amy = fmaxf(amy, __shfl_xor_sync(0xffffffffu, amy, o));
-  }
-  const int anybad = __syncthreads_or(bad ? 1 : 0);
-  if (lane == 0) {
-    s_red[0][warp] = amx;
-    s_red[1][warp] = amy;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    for (int w = 1; w < NT / 32; ++w) {
-      amx = fmaxf(amx, s_red[0][w]);
-      amy = fmaxf(amy, s_red[1][w]);
+    for (int o = 16; o > 0; o >>= 1) {
+      amx = fmaxf(amx, __shfl_xor_sync(0xffffffffu, amx, o));
+      amy = fmaxf(amy, __shfl_xor_sync(0xffffffffu, amy, o));
     }
-    if (anybad) atomicOr(&st->err, 1);
-    if (p.write_slot >= 0) {
-      atomicMax(&st->alpha_bits[p.write_slot][0], double_to_bits((double)amx));
-      atomicMax(&st->alpha_bits[p.write_slot][1], double_to_bits((double)amy));
+    const int anybad = __syncthreads_or(bad ? 1 : 0);
+    if (lane == 0) {
+      s_red[0][warp] = amx;
+      s_red[1][warp] = amy;
     }
-    __threadfence();
-    const unsigned int prev = atomicAdd(&st->counter, 1u);
-    s_last = (prev == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (s_last && tid == 0) {
-    __threadfence();
-    st->counter = 0;
-    if (p.zero_slot >= 0) {
-      st->alpha_bits[p.zero_slot][0] = 0ull;
-      st->alpha_bits[p.zero_slot][1] = 0ull;
-    }
-    if (p.stage == 1 && p.loop_mode != LOOP_STAGE) {
-      st->dt = s_dt;
-      st->last = s_lastflag;
-    }
-    if (p.stage == 3) {
-      if (PREC == P_MIXED) st->cur = cur ^ 1;
-      if (p.loop_mode != LOOP_STAGE) {
-        st->t = st->last ? st->t_final : st->t + st->dt;
-        st->steps += 1;
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < NT / 32; ++w) {
+        amx = fmaxf(amx, s_red[0][w]);
+        amy = fmaxf(amy, s_red[1][w]);
+      }
+      DevState *st = d.st;
+      if (anybad) atomicOr(&st->err, 1);
+      if (p.write_slot >= 0) {
+        atomicMax(&st->alpha_bits[p.write_slot][0], double_to_bits((double)amx));
+        atomicMax(&st->alpha_bits[p.write_slot][1], double_to_bits((double)amy));
+      }
+      __threadfence();
+      const unsigned int prev = atomicAdd(&st->counter, 1u);
+      if (prev == (unsigned int)d.ntiles - 1u) {
+        // every tile of this instance has finished this stage
+        __threadfence();
+        st->counter = 0;
+        if (p.zero_slot >= 0) {
+          st->alpha_bits[p.zero_slot][0] = 0ull;
+          st->alpha_bits[p.zero_slot][1] = 0ull;
+        }
+        if (p.stage == 1 && p.loop_mode != LOOP_STAGE) {
+          st->dt = info.dt;
+          st->last = info.last;
+        }
+        if (p.stage == 3) {
+          if (PREC == P_MIXED) st->cur = info.cur ^ 1;
+          if (p.loop_mode != LOOP_STAGE) {
+            const double tn = st->last ? st->t_final : st->t + st->dt;
+            st->t = tn;
+            st->steps += 1;
+            if (p.loop_mode == LOOP_STEP_TO && !(tn < st->t_final) && prm.done_count) atomicAdd(prm.done_count, 1);
+          }
+        }
       }
     }
+    __syncthreads();  // raw[buf], dX, dY, su, s_info[buf] are free for the next tile
   }
 }
 

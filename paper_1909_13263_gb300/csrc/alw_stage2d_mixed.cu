@@ -3,4 +3,5 @@
 
 namespace alw {
 int launch_stage2d_mixed(const Stage2DParams &prm, void *stream) { return launch2d_impl<P_MIXED>(prm, stream); }
+int stage2d_grid_cap_mixed(int weights) { return grid_cap_impl<P_MIXED>(weights); }
 }  // namespace alw

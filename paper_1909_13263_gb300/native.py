@@ -63,6 +63,13 @@ class State(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("steps", ctypes.c_int64), ("alpha", ctypes.c_double * 2)]
 
 
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int32), ("steps_per_graph", ctypes.c_int32), ("grid_ctas", ctypes.c_int32)]
+
+
+ORDER = {"instance": 0, "largest_first": 1, "interleaved": 2}
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -112,6 +119,16 @@ def load():
             "alw_memory_bytes": (ctypes.c_int, [P, ctypes.POINTER(SZ)]),
             "alw_step_noalloc": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Hamiltonian),
                                                 ctypes.POINTER(Scheme), P, P, D, I32, P]),
+            "alw_batch_create": (ctypes.c_int, [ctypes.POINTER(Scheme), P, ctypes.POINTER(P)]),
+            "alw_batch_add": (ctypes.c_int, [P, ctypes.POINTER(Grid), ctypes.POINTER(Hamiltonian), P, SZ, D,
+                                             ctypes.POINTER(I32)]),
+            "alw_batch_set_tuning": (ctypes.c_int, [P, ctypes.POINTER(BatchTuning)]),
+            "alw_batch_get_tuning": (ctypes.c_int, [P, ctypes.POINTER(BatchTuning)]),
+            "alw_batch_run": (ctypes.c_int, [P, ctypes.POINTER(I64)]),
+            "alw_batch_get_phi": (ctypes.c_int, [P, I32, P, SZ]),
+            "alw_batch_get_state": (ctypes.c_int, [P, I32, ctypes.POINTER(State)]),
+            "alw_batch_memory_bytes": (ctypes.c_int, [P, ctypes.POINTER(SZ)]),
+            "alw_batch_destroy": (ctypes.c_int, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -285,3 +302,79 @@ def step_noalloc(phi_in, phi_out, *, dim: int, nx: int, ny: int = 1, bc: str = "
                              ctypes.c_void_p(phi_out.data_ptr()), float(dt), int(nsteps),
                              ctypes.c_void_p(_stream_handle(stream))))
     return phi_out
+
+
+class Batch:
+    """Many independent 2D periodic instances advanced together (alw_batch_*)."""
+
+    def __init__(self, *, weights: str = "arclength", precision: str = "mixed", eps: float = 1e-6, cfl: float = 0.6,
+                 dt_mode: str = "cfl", alpha_mode: str = "default", alpha_fixed=(0.0, 0.0), stream=None):
+        self._L = load()
+        self.scheme = Scheme(WEIGHTS[weights], eps, cfl, DT[dt_mode], ALPHA[alpha_mode],
+                             (ctypes.c_double * 2)(*alpha_fixed), PREC[precision])
+        h = ctypes.c_void_p()
+        check(self._L.alw_batch_create(ctypes.byref(self.scheme), ctypes.c_void_p(_stream_handle(stream)),
+                                       ctypes.byref(h)))
+        self._h = h
+        self.shapes = []
+
+    def add(self, *, nx: int, ny: int, xlo: float, xhi: float, ylo: float, yhi: float, ham: str, phi0,
+            t_final: float) -> int:
+        g = Grid(2, nx, ny, BC["periodic"], xlo, xhi, ylo, yhi)
+        hm = Hamiltonian(HAM[ham], (ctypes.c_double * 4)(0, 0, 0, 0))
+        a = np.ascontiguousarray(phi0, dtype=np.float64)
+        i = ctypes.c_int32()
+        check(self._L.alw_batch_add(self._h, ctypes.byref(g), ctypes.byref(hm), a.ctypes.data, a.size,
+                                    float(t_final), ctypes.byref(i)))
+        self.shapes.append((ny, nx))
+        return i.value
+
+    def set_tuning(self, order: str = None, steps_per_graph: int = 4, grid_ctas: int = 0):
+        if order is None:
+            check(self._L.alw_batch_set_tuning(self._h, None))
+            return
+        t = BatchTuning(ORDER[order], steps_per_graph, grid_ctas)
+        check(self._L.alw_batch_set_tuning(self._h, ctypes.byref(t)))
+
+    def tuning(self) -> dict:
+        t = BatchTuning()
+        check(self._L.alw_batch_get_tuning(self._h, ctypes.byref(t)))
+        inv = {v: k for k, v in ORDER.items()}
+        return {"order": inv.get(t.order, t.order), "steps_per_graph": t.steps_per_graph, "grid_ctas": t.grid_ctas}
+
+    def run(self) -> int:
+        r = ctypes.c_int64()
+        check(self._L.alw_batch_run(self._h, ctypes.byref(r)))
+        return r.value
+
+    def get_phi(self, i: int) -> np.ndarray:
+        out = np.empty(self.shapes[i], dtype=np.float64)
+        check(self._L.alw_batch_get_phi(self._h, int(i), out.ctypes.data, out.size))
+        return out
+
+    def get_state(self, i: int) -> State:
+        st = State()
+        check(self._L.alw_batch_get_state(self._h, int(i), ctypes.byref(st)))
+        return st
+
+    def memory_bytes(self) -> int:
+        b = ctypes.c_size_t()
+        check(self._L.alw_batch_memory_bytes(self._h, ctypes.byref(b)))
+        return b.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.alw_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
