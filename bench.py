@@ -204,6 +204,100 @@ def run_reference(args):
     return 0
 
 
+def _latency_summary(lat):
+    import numpy as np
+
+    a = np.asarray(lat)
+    return {"p50_s": float(np.percentile(a, 50)), "p99_s": float(np.percentile(a, 99)),
+            "mean_s": float(a.mean())}
+
+
+def bench_batched(args, stream):
+    """512 instances of uneven size (64^2..1024^2, two Hamiltonians, phase-shifted phi0, own
+    t_final), host to host: one batch vs a loop of one-at-a-time solves."""
+    from paper_1909_13263_gb300 import inputs, native
+
+    insts = inputs.batch_instances(args.batch_count, 64, 1024)
+    phis = [inputs.instance_phi0(i)[0] for i in insts]
+    kw = dict(xlo=-2.0, xhi=2.0, ylo=-2.0, yhi=2.0)
+    node_steps = 0
+    t0 = time.perf_counter()
+    with native.Batch(precision="mixed", weights=args.weights, stream=stream) as b:
+        for inst, ph in zip(insts, phis):
+            b.add(nx=inst.n, ny=inst.n, ham=inst.ham, phi0=ph, t_final=inst.t_final, **kw)
+        replays = b.run()
+        outs = [b.get_phi(k) for k in range(len(insts))]
+        for k, inst in enumerate(insts):
+            node_steps += inst.n * inst.n * b.get_state(k).steps
+        tuning = b.tuning()
+        mem = b.memory_bytes()
+    t_batch = time.perf_counter() - t0
+    serial_n = min(len(insts), args.serial_count)
+    t0 = time.perf_counter()
+    for inst, ph in list(zip(insts, phis))[:serial_n]:
+        with native.Solver(dim=2, nx=inst.n, ny=inst.n, ham=inst.ham, precision="mixed", weights=args.weights,
+                           stream=stream, **kw) as s:
+            s.set_phi0(ph)
+            s.step_to(inst.t_final)
+            s.get_phi()
+    t_serial = time.perf_counter() - t0
+    ok = all(bool((o == o).all()) for o in outs)
+    return {"instances": len(insts), "solves_per_s": len(insts) / t_batch,
+            "serial_solves_per_s": serial_n / t_serial, "speedup_vs_serial": (len(insts) / t_batch) / (serial_n / t_serial),
+            "point_updates_per_s": node_steps / t_batch, "wall_s": t_batch, "graph_replays": replays,
+            "tuning": tuning, "device_bytes": mem, "serial_sample": serial_n, "finite": ok}
+
+
+def bench_serving(args, stream, rate):
+    """Poisson arrivals of solves (128^2..2048^2, the batch mix) into the continuous-batching server
+    under an HBM budget; latency from arrival to result, against one-at-a-time plain solves."""
+    import threading
+
+    from paper_1909_13263_gb300 import inputs, native
+
+    reqs = inputs.request_stream(rate, args.serve_count, 128, 2048)
+    phis = [inputs.instance_phi0(i)[0] for _, i in reqs]
+    kw = dict(xlo=-2.0, xhi=2.0, ylo=-2.0, yhi=2.0)
+    with native.Server(hbm_budget_bytes=int(args.serve_budget_gb * 2**30), max_slots=256, max_side=2048,
+                       weights=args.weights, stream=stream) as srv:
+        srv.set_round_steps(args.serve_round_steps)
+        ids = [None] * len(reqs)
+        t0 = time.perf_counter()
+        for k, ((at, inst), ph) in enumerate(zip(reqs, phis)):
+            delay = t0 + at - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            ids[k] = srv.submit(nx=inst.n, ny=inst.n, ham=inst.ham, phi0=ph, t_final=inst.t_final, **kw)
+        lat = []
+        for rid in ids:
+            done, info, _ = srv.poll(rid, timeout=600.0, fetch=True)
+            lat.append(info["latency_s"])
+        makespan = time.perf_counter() - t0
+        rounds = srv.stats()["rounds"]
+    served = {"rate_per_s": rate, "requests": len(reqs), "solves_per_s": len(reqs) / makespan,
+              "rounds": rounds, "round_steps": args.serve_round_steps, **_latency_summary(lat)}
+    # one-at-a-time plain solves of the same arrivals (FIFO, a single worker)
+    lat_s = []
+    done_at = 0.0
+    t0 = time.perf_counter()
+    for (at, inst), ph in zip(reqs, phis):
+        delay = t0 + at - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        with native.Solver(dim=2, nx=inst.n, ny=inst.n, ham=inst.ham, precision="mixed", weights=args.weights,
+                           stream=stream, **kw) as s:
+            s.set_phi0(ph)
+            s.step_to(inst.t_final)
+            s.get_phi()
+        done_at = time.perf_counter() - t0
+        lat_s.append(done_at - at)
+    serial = {"solves_per_s": len(reqs) / done_at, **_latency_summary(lat_s)}
+    return {"served": served, "serial": serial,
+            "p99_speedup_vs_serial": serial["p99_s"] / served["p99_s"],
+            "solves_per_s_vs_serial": served["solves_per_s"] / serial["solves_per_s"],
+            "budget_gb": args.serve_budget_gb}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -280,6 +374,14 @@ def run_ours(args):
                "finite": bool(np.isfinite(phi).all())}
         del phi0_host, phi
 
+    batched = serving = None
+    if not args.no_batch:
+        with torch.cuda.stream(stream):
+            batched = bench_batched(args, stream)
+    if not args.no_serve:
+        with torch.cuda.stream(stream):
+            serving = bench_serving(args, stream, args.serve_rate)
+
     if rank != 0:
         return 0
     peaks, src = _peaks()
@@ -328,6 +430,8 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": 3 * args.steps,
         "clocks": clocks,
+        "batched": batched,
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:
@@ -349,6 +453,14 @@ def main():
     ap.add_argument("--cpu-n", type=int, default=512)
     ap.add_argument("--cpu-steps", type=int, default=20)
     ap.add_argument("--ref-n", type=int, default=128)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--serial-count", type=int, default=128)
+    ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--serve-round-steps", type=int, default=4)
+    ap.add_argument("--serve-count", type=int, default=120)
+    ap.add_argument("--serve-budget-gb", type=float, default=60.0)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -238,6 +238,48 @@ alw_status alw_batch_memory_bytes(alw_batch *b, size_t *bytes);
 alw_status alw_batch_destroy(alw_batch *b);
 
 /* ------------------------------------------------------------------------
+ * Serving: a request loop with continuous batching.  Submitted solves (2D,
+ * periodic, FP32 or MIXED, grid sides up to max_side) wait in a FIFO queue; a
+ * host worker thread admits them at round boundaries while a slot and enough
+ * of the device-memory budget are free (state stays resident on the device),
+ * advances every resident instance by a few RK3 steps per round in shared
+ * persistent launches (their stages interleave), and retires each instance
+ * when it reaches its t_final.  Each result equals the single solve of the
+ * same request.  Not a construct of the paper. */
+typedef struct alw_server alw_server;
+
+typedef struct {
+  int32_t status;     /* ALW_OK or the request's error */
+  int64_t steps;      /* RK3 steps taken */
+  double queue_s;     /* submit -> admission */
+  double latency_s;   /* submit -> result available */
+} alw_request_info;
+
+typedef struct {
+  int64_t submitted, admitted, completed, queued, rounds;
+  int64_t arena_rows, free_rows;  /* device arena rows in total / free now */
+} alw_server_stats;
+
+/* hbm_budget_bytes bounds all device memory the server holds (arena of
+ * resident instances + tables + staging); ALW_EBUDGET if it cannot hold one
+ * instance of max_side x max_side.  max_slots bounds resident instances. */
+alw_status alw_server_create(const alw_scheme *scheme, size_t hbm_budget_bytes, int32_t max_slots, int32_t max_side,
+                             void *cuda_stream, alw_server **out);
+/* RK3 steps each resident instance takes per round (admission granularity). */
+alw_status alw_server_set_round_steps(alw_server *s, int32_t steps);
+/* Queue a solve (host_phi0 copied); req_id receives its id. */
+alw_status alw_server_submit(alw_server *s, const alw_grid *grid, const alw_hamiltonian *ham, const double *host_phi0,
+                             size_t n, double t_final, uint64_t *req_id);
+/* Wait up to timeout_s (0: do not wait) for a request.  done = 1 when finished;
+ * then info (nullable) is filled and, if host_out is given (n values), the
+ * result is copied and the request is forgotten. */
+alw_status alw_server_poll(alw_server *s, uint64_t req_id, double timeout_s, int32_t *done, double *host_out,
+                           size_t n, alw_request_info *info);
+alw_status alw_server_stats_get(alw_server *s, alw_server_stats *stats);
+/* Stops the worker after its current round and frees everything. */
+alw_status alw_server_destroy(alw_server *s);
+
+/* ------------------------------------------------------------------------
  * No-allocation entry point (the paper has no counterpart; it serves callers
  * that cannot obtain device memory on demand, e.g. a framework whose pool
  * allocator owns all device memory, or a real-time loop that must not

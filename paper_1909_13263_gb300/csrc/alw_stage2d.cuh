@@ -14,9 +14,11 @@
 //      writes phi_x^-/+ to shared memory;
 //   3. y sweep: each lane takes 8 consecutive nodes of one column, forms the
 //      Lax-Friedrichs Hamiltonian and the RK combination, and stores.
-// After each tile the CTA folds max |dH/dp|, |dH/dq| into the instance's slot;
-// the CTA that completes an instance's last tile closes the instance's stage
-// (dt, time, step count, buffer flip), so instances advance independently.
+// A CTA keeps running maxima of |dH/dp|, |dH/dq| over consecutive tiles of
+// one instance and folds them into the instance's slot (with the number of
+// tiles done) when the instance changes; the CTA that completes an instance's
+// last tile closes the instance's stage (dt, time, step count, buffer flip),
+// so instances advance independently.
 #pragma once
 #include "alw_device.cuh"
 #include "alw_params2d.h"
@@ -135,6 +137,7 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
   float2 *su = reinterpret_cast<float2 *>(dY + DYH * TX);  // [TY][SUP] (offset is an even float count)
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ TileInfo s_info[2];
+  __shared__ TileInfo s_pinfo;  // thread 0's last prepared tile (per-instance scalars reused while it repeats)
   __shared__ float s_red[2][NT / 32];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -145,7 +148,28 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
 
   auto desc = [&](int inst) -> const InstDesc & { return batch ? prm.insts[inst] : prm.inst0; };
 
-  // thread 0: decode work-list entry t, compute its instance's stage scalars, issue its loads into buffer b
+  // thread 0: one TMA box per array of the tile (with halo) into buffer b
+  auto issue_loads = [&](const TileInfo &info, const InstDesc &d, int b) {
+    const CUtensorMap *mA, *mB = nullptr, *mC = nullptr;
+    if (PREC == P_MIXED) {
+      mA = &prm.maps[prm.map_a + info.cur];
+      mB = &prm.maps[prm.map_b + info.cur];
+      if (prm.map_c >= 0) mC = &prm.maps[prm.map_c];
+    } else {
+      mA = &prm.maps[prm.map_a];
+      if (prm.map_b >= 0) mB = &prm.maps[prm.map_b];
+    }
+    const int nm = 1 + (mB != nullptr) + (mC != nullptr);
+    float *dst = raw + b * NARR * ARR;
+    const int y = d.row_off + info.ty0;
+    mbar_arrive_expect_tx(&bars[b], box_bytes * nm);
+    tma_load_2d(dst, mA, info.tx0, y, &bars[b]);
+    if (mB) tma_load_2d(dst + ARR, mB, info.tx0, y, &bars[b]);
+    if (mC) tma_load_2d(dst + 2 * ARR, mC, info.tx0, y, &bars[b]);
+  };
+
+  // thread 0: decode work-list entry t, compute its instance's stage scalars (reused while the
+  // instance repeats), issue its loads into buffer b
   auto prepare = [&](int t, int b) {
     int inst = 0, tl = t;
     if (batch) {
@@ -156,6 +180,15 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
     const InstDesc &d = desc(inst);
     const DevState *st = d.st;
     TileInfo info;
+    if (inst == s_pinfo.inst) {
+      info = s_pinfo;
+      info.tx0 = (tl % d.tiles_x) * TX;
+      info.ty0 = (tl / d.tiles_x) * TY;
+      s_info[b] = info;
+      s_pinfo = info;
+      if (!info.skip) issue_loads(info, d, b);
+      return;
+    }
     info.inst = inst;
     info.tx0 = (tl % d.tiles_x) * TX;
     info.ty0 = (tl / d.tiles_x) * TY;
@@ -197,35 +230,25 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
     info.fax = fax;
     info.fay = fay;
     s_info[b] = info;
-    if (info.skip) return;
-    const CUtensorMap *mA, *mB = nullptr, *mC = nullptr;
-    if (PREC == P_MIXED) {
-      mA = &prm.maps[prm.map_a + info.cur];
-      mB = &prm.maps[prm.map_b + info.cur];
-      if (prm.map_c >= 0) mC = &prm.maps[prm.map_c];
-    } else {
-      mA = &prm.maps[prm.map_a];
-      if (prm.map_b >= 0) mB = &prm.maps[prm.map_b];
-    }
-    const int nm = 1 + (mB != nullptr) + (mC != nullptr);
-    float *dst = raw + b * NARR * ARR;
-    const int y = d.row_off + info.ty0;
-    mbar_arrive_expect_tx(&bars[b], box_bytes * nm);
-    tma_load_2d(dst, mA, info.tx0, y, &bars[b]);
-    if (mB) tma_load_2d(dst + ARR, mB, info.tx0, y, &bars[b]);
-    if (mC) tma_load_2d(dst + 2 * ARR, mC, info.tx0, y, &bars[b]);
+    s_pinfo = info;
+    if (!info.skip) issue_loads(info, d, b);
   };
 
   if (tid == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
     fence_mbar_init();
+    s_pinfo.inst = -1;
     if ((int)blockIdx.x < ntiles) prepare(blockIdx.x, 0);
   }
   __syncthreads();
 
   uint32_t phase = 0;  // bit b: parity of the next completion of bars[b]
   int k = 0;
+  // running alpha maxima and tile count of the current run of same-instance tiles
+  float amx = 0.0f, amy = 0.0f;
+  bool bad = false;
+  int run_tiles = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
     const int buf = k & 1;
     const int next = t + gridDim.x;
@@ -233,8 +256,8 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
       fence_proxy_async_smem();
       prepare(next, buf ^ 1);
     }
-    const TileInfo info = s_info[buf];
-    if (info.skip) {
+    const int i_inst = s_info[buf].inst, i_skip = s_info[buf].skip, i_cur = s_info[buf].cur;
+    if (i_skip) {
       __syncthreads();
       continue;
     }
@@ -242,7 +265,7 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
     if (__syncthreads_or(!ok)) {
       // a tile load never completed: flag the instance, let the other in-flight load land, stop
       if (tid == 0) {
-        atomicOr(&desc(info.inst).st->err, 2);
+        atomicOr(&desc(i_inst).st->err, 2);
         if (next < ntiles && !s_info[buf ^ 1].skip) mbar_wait_bounded(&bars[buf ^ 1], (phase >> (buf ^ 1)) & 1u);
       }
       __syncthreads();
@@ -250,11 +273,11 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
     }
     phase ^= 1u << buf;
 
-    const InstDesc &d = desc(info.inst);
-    const int nx = d.nx, ny = d.ny, tx0 = info.tx0, ty0 = info.ty0;
+    const InstDesc &d = desc(i_inst);
+    const int nx = d.nx, ny = d.ny, tx0 = s_info[buf].tx0, ty0 = s_info[buf].ty0;
     const size_t rbase = (size_t)d.row_off * p.pitch;   // element offset of the instance's rows
     const HamSel<H> ham{d.ham};
-    const float dtf = info.dtf, fax = info.fax, fay = info.fay;
+    const float dtf = s_info[buf].dtf, fax = s_info[buf].fax, fay = s_info[buf].fay;
     const float *A = raw + buf * NARR * ARR;
     const float *B = A + ARR;
     const float *C = A + 2 * ARR;
@@ -286,8 +309,6 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
 
     const bool edge = (tx0 < 3) || (tx0 + TX > nx - 3) || (ty0 < 3) || (ty0 + TY > ny - 3);
     const int colY = ((warp & 1) << 5) + lane, segY = warp >> 1;
-    float amx = 0.0f, amy = 0.0f;
-    bool bad = false;
 
     // ---- 2./3. sweeps (one code path for both directions)
 #pragma unroll 1
@@ -323,8 +344,8 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
             const float dd = (2.0f / 3.0f) * fmaf(dtf, L, C[sidx]);
             float h, l;
             df_add(A[sidx], B[sidx], dd, h, l);
-            float *oh = reinterpret_cast<float *>(p.mix_hi[info.cur ^ 1]);
-            float *ol = reinterpret_cast<float *>(p.mix_lo[info.cur ^ 1]);
+            float *oh = reinterpret_cast<float *>(p.mix_hi[i_cur ^ 1]);
+            float *ol = reinterpret_cast<float *>(p.mix_lo[i_cur ^ 1]);
             if (edge) {
               store_node<float, 2>(oh + rbase, p.pitch, nx, ny, d.bc, gi, gj, h);
               store_node<float, 2>(ol + rbase, p.pitch, nx, ny, d.bc, gi, gj, l);
@@ -357,7 +378,14 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
       if (dir == 0) __syncthreads();
     }
 
-    // ---- this tile's maximum of alpha into the instance's slot; close the instance's stage
+    // ---- when the next tile of this CTA belongs to another instance (or there is none), fold the
+    // run's maximum of alpha into the instance's slot and count its tiles; close the instance's stage
+    ++run_tiles;
+    const bool more = next < ntiles;
+    if (more && !s_info[buf ^ 1].skip && s_info[buf ^ 1].inst == i_inst) {
+      __syncthreads();  // raw[buf], dX, dY, su are free for the next tile
+      continue;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       amx = fmaxf(amx, __shfl_xor_sync(0xffffffffu, amx, o));
@@ -381,8 +409,8 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
         atomicMax(&st->alpha_bits[p.write_slot][1], double_to_bits((double)amy));
       }
       __threadfence();
-      const unsigned int prev = atomicAdd(&st->counter, 1u);
-      if (prev == (unsigned int)d.ntiles - 1u) {
+      const unsigned int prev = atomicAdd(&st->counter, (unsigned int)run_tiles);
+      if (prev + (unsigned int)run_tiles == (unsigned int)d.ntiles) {
         // every tile of this instance has finished this stage
         __threadfence();
         st->counter = 0;
@@ -391,11 +419,11 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
           st->alpha_bits[p.zero_slot][1] = 0ull;
         }
         if (p.stage == 1 && p.loop_mode != LOOP_STAGE) {
-          st->dt = info.dt;
-          st->last = info.last;
+          st->dt = s_info[buf].dt;
+          st->last = s_info[buf].last;
         }
         if (p.stage == 3) {
-          if (PREC == P_MIXED) st->cur = info.cur ^ 1;
+          if (PREC == P_MIXED) st->cur = i_cur ^ 1;
           if (p.loop_mode != LOOP_STAGE) {
             const double tn = st->last ? st->t_final : st->t + st->dt;
             st->t = tn;
@@ -405,6 +433,9 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
         }
       }
     }
+    amx = amy = 0.0f;
+    bad = false;
+    run_tiles = 0;
     __syncthreads();  // raw[buf], dX, dY, su, s_info[buf] are free for the next tile
   }
 }

@@ -70,6 +70,17 @@ class BatchTuning(ctypes.Structure):
 ORDER = {"instance": 0, "largest_first": 1, "interleaved": 2}
 
 
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("steps", ctypes.c_int64), ("queue_s", ctypes.c_double),
+                ("latency_s", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("rounds", ctypes.c_int64), ("arena_rows", ctypes.c_int64),
+                ("free_rows", ctypes.c_int64)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -129,6 +140,14 @@ def load():
             "alw_batch_get_state": (ctypes.c_int, [P, I32, ctypes.POINTER(State)]),
             "alw_batch_memory_bytes": (ctypes.c_int, [P, ctypes.POINTER(SZ)]),
             "alw_batch_destroy": (ctypes.c_int, [P]),
+            "alw_server_create": (ctypes.c_int, [ctypes.POINTER(Scheme), SZ, I32, I32, P, ctypes.POINTER(P)]),
+            "alw_server_set_round_steps": (ctypes.c_int, [P, I32]),
+            "alw_server_submit": (ctypes.c_int, [P, ctypes.POINTER(Grid), ctypes.POINTER(Hamiltonian), P, SZ, D,
+                                                 ctypes.POINTER(ctypes.c_uint64)]),
+            "alw_server_poll": (ctypes.c_int, [P, ctypes.c_uint64, D, ctypes.POINTER(I32), P, SZ,
+                                               ctypes.POINTER(RequestInfo)]),
+            "alw_server_stats_get": (ctypes.c_int, [P, ctypes.POINTER(ServerStats)]),
+            "alw_server_destroy": (ctypes.c_int, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -365,6 +384,73 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             self._L.alw_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Server:
+    """Continuous-batching request loop (alw_server_*)."""
+
+    def __init__(self, *, hbm_budget_bytes: int, max_slots: int = 256, max_side: int = 2048,
+                 weights: str = "arclength", precision: str = "mixed", eps: float = 1e-6, cfl: float = 0.6,
+                 alpha_mode: str = "default", stream=None):
+        self._L = load()
+        self.scheme = Scheme(WEIGHTS[weights], eps, cfl, DT["cfl"], ALPHA[alpha_mode], (ctypes.c_double * 2)(0, 0),
+                             PREC[precision])
+        h = ctypes.c_void_p()
+        check(self._L.alw_server_create(ctypes.byref(self.scheme), int(hbm_budget_bytes), int(max_slots),
+                                        int(max_side), ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(h)))
+        self._h = h
+        self.shapes = {}
+
+    def set_round_steps(self, steps: int):
+        check(self._L.alw_server_set_round_steps(self._h, int(steps)))
+
+    def submit(self, *, nx: int, ny: int, xlo: float, xhi: float, ylo: float, yhi: float, ham: str, phi0,
+               t_final: float) -> int:
+        g = Grid(2, nx, ny, BC["periodic"], xlo, xhi, ylo, yhi)
+        hm = Hamiltonian(HAM[ham], (ctypes.c_double * 4)(0, 0, 0, 0))
+        a = np.ascontiguousarray(phi0, dtype=np.float64)
+        rid = ctypes.c_uint64()
+        check(self._L.alw_server_submit(self._h, ctypes.byref(g), ctypes.byref(hm), a.ctypes.data, a.size,
+                                        float(t_final), ctypes.byref(rid)))
+        self.shapes[rid.value] = (ny, nx)
+        return rid.value
+
+    def poll(self, rid: int, timeout: float = 0.0, fetch: bool = True):
+        """(done, info dict, result or None); with fetch the result is copied out and the request forgotten."""
+        done = ctypes.c_int32()
+        info = RequestInfo()
+        out = np.empty(self.shapes[rid], dtype=np.float64) if fetch else None
+        check(self._L.alw_server_poll(self._h, ctypes.c_uint64(rid), float(timeout), ctypes.byref(done),
+                                      out.ctypes.data if (fetch and out is not None) else None,
+                                      out.size if fetch else 0, ctypes.byref(info)))
+        if not done.value:
+            return False, None, None
+        d = {"status": info.status, "steps": info.steps, "queue_s": info.queue_s, "latency_s": info.latency_s}
+        if fetch:
+            self.shapes.pop(rid, None)
+        return True, d, out
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        check(self._L.alw_server_stats_get(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.alw_server_destroy(self._h)
             self._h = None
 
     def __del__(self):
