@@ -272,11 +272,9 @@ __device__ __forceinline__ void df_add(float hi, float lo, float d, float &ohi, 
 // Store one output value at interior node (gi, gj) and at every periodic ghost
 // position that holds a copy of it (a cross-shaped stencil never reads corners).
 template <typename S, int DIM>
-__device__ __forceinline__ void store_node(S *arr, int pitch, int nx, int ny, int bc, int gi, int gj, S val) {
+__device__ __noinline__ void store_ghosts(S *arr, int pitch, int nx, int ny, int gi, int gj, S val) {
   const int gy = (DIM == 2) ? GY : 0;
   S *row = arr + (size_t)(gj + gy) * pitch;
-  row[gi + GX] = val;
-  if (bc != BC_PERIODIC) return;
   if (gi < 3 || gi >= nx - 3) {
 #pragma unroll
     for (int k = 1; k <= 3; ++k) {
@@ -297,6 +295,15 @@ __device__ __forceinline__ void store_node(S *arr, int pitch, int nx, int ny, in
       if (w == gj) arr[(size_t)(g + GY) * pitch + gi + GX] = val;
     }
   }
+}
+
+template <typename S, int DIM>
+__device__ __forceinline__ void store_node(S *arr, int pitch, int nx, int ny, int bc, int gi, int gj, S val) {
+  const int gy = (DIM == 2) ? GY : 0;
+  arr[(size_t)(gj + gy) * pitch + gi + GX] = val;
+  if (bc != BC_PERIODIC) return;
+  if (gi < 3 || gi >= nx - 3 || (DIM == 2 && (gj < 3 || gj >= ny - 3)))
+    store_ghosts<S, DIM>(arr, pitch, nx, ny, gi, gj, val);
 }
 
 }  // namespace alw

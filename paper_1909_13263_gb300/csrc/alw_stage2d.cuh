@@ -9,11 +9,13 @@
 // tile:
 //   1. differences pass: Delta^+ phi along x (dX) and y (dY) for every cell,
 //      combining the MIXED parts (hi + lo + delta) once per cell;
-//   2. x sweep: warp w takes nodes 8w..8w+7 of every row (one row per lane;
-//      the odd dX pitch makes these column-wise reads conflict-free) and
-//      writes phi_x^-/+ to shared memory;
-//   3. y sweep: each lane takes 8 consecutive nodes of one column, forms the
-//      Lax-Friedrichs Hamiltonian and the RK combination, and stores.
+//   2. both sweeps in one pass, packed two lanes per value (f32x2): each
+//      thread sweeps nodes 8w..8w+7 of row `lane` along x (warp w; the odd dX
+//      pitch makes these column-wise reads conflict-free) in lane .x and 8
+//      consecutive nodes of one column along y in lane .y; phi_x^-/+ go to
+//      shared memory, phi_y^-/+ stay in registers;
+//   3. each thread forms, for its 8 column nodes, the Lax-Friedrichs
+//      Hamiltonian and the RK combination, and stores.
 // A CTA keeps running maxima of |dH/dp|, |dH/dq| over consecutive tiles of
 // one instance and folds them into the instance's slot (with the number of
 // tiles done) when the instance changes; the CTA that completes an instance's
@@ -310,72 +312,79 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
     const bool edge = (tx0 < 3) || (tx0 + TX > nx - 3) || (ty0 < 3) || (ty0 + TY > ny - 3);
     const int colY = ((warp & 1) << 5) + lane, segY = warp >> 1;
 
-    // ---- 2./3. sweeps (one code path for both directions)
-#pragma unroll 1
-    for (int dir = 0; dir < 2; ++dir) {
-      const float *vsrc = dir == 0 ? dX + lane * DXP + K * warp : dY + (K * segY) * TX + colY;
-      const int vstride = dir == 0 ? 1 : TX;
-      auto v_at = [&](int m) { return vsrc[m * vstride]; };
-      auto emit = [&](int q, float dmq, float dpq) {
-        if (dir == 0) {
-          su[lane * SUP + K * warp + q] = make_float2(dmq, dpq);
-          return;
-        }
-        // node (colY, y) of the tile: phi_y^-/+ = (dmq, dpq)
-        const int y = K * segY + q;
-        const int gi = tx0 + colY, gj = ty0 + y;
-        const bool inside = !edge || (gi < nx && gj < ny);
-        const float2 u = su[y * SUP + colY];
-        float ax, ay;
-        ham.alpha(u.x, u.y, dmq, dpq, ax, ay);
-        if (inside) {
-          if (!isfinite(u.x + u.y + dmq + dpq)) bad = true;
-          amx = fmaxf(amx, ax);
-          amy = fmaxf(amy, ay);
-        }
-        if (p.stage == 0 || !inside) return;
-        const float aX = local_alpha ? ax : fax, aY = local_alpha ? ay : fay;
-        const float Hv = ham.value(0.5f * (u.y + u.x), 0.5f * (dpq + dmq));
-        const float L = fmaf(aX * 0.5f, u.y - u.x, fmaf(aY * 0.5f, dpq - dmq, -Hv));
-        const int sidx = (y + 3) * SW + colY + 4;
-        const size_t g = rbase + (size_t)(gj + GY) * p.pitch + gi + GX;
-        if (PREC == P_MIXED) {
-          if (p.stage == 3) {
-            const float dd = (2.0f / 3.0f) * fmaf(dtf, L, C[sidx]);
-            float h, l;
-            df_add(A[sidx], B[sidx], dd, h, l);
-            float *oh = reinterpret_cast<float *>(p.mix_hi[i_cur ^ 1]);
-            float *ol = reinterpret_cast<float *>(p.mix_lo[i_cur ^ 1]);
-            if (edge) {
-              store_node<float, 2>(oh + rbase, p.pitch, nx, ny, d.bc, gi, gj, h);
-              store_node<float, 2>(ol + rbase, p.pitch, nx, ny, d.bc, gi, gj, l);
-            } else {
-              oh[g] = h;
-              ol[g] = l;
-            }
+    // ---- 2. both sweeps in one pass: each thread's row segment (x, lane .x of the packed values)
+    // and column segment (y, lane .y) run the same instruction stream
+    float ym[K], yp[K];
+    {
+      const float *vx = dX + lane * DXP + K * warp;
+      const float *vy = dY + (K * segY) * TX + colY;
+      auto v_at = [&](int m) { return make_float2(vx[m], vy[m * TX]); };
+      auto emit = [&](int q, float2 dm, float2 dp) {
+        su[lane * SUP + K * warp + q] = make_float2(dm.x, dp.x);
+        ym[q] = dm.y;
+        yp[q] = dp.y;
+      };
+      const float2 rd = make_float2(d.rdx, d.rdy);
+      const float2 e4 = make_float2(4.0f * eps * d.rdx * d.rdx, 4.0f * eps * d.rdy * d.rdy);
+      sweep_stream<K, W, float2>(v_at, rd, e4, make_float2(eps, eps), emit);
+    }
+    __syncthreads();
+
+    // ---- 3. nodes (colY, K*segY + q): Lax-Friedrichs Hamiltonian, RK combination, store
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const float dmq = ym[q], dpq = yp[q];
+      const int y = K * segY + q;
+      const int gi = tx0 + colY, gj = ty0 + y;
+      const bool inside = !edge || (gi < nx && gj < ny);
+      const float2 u = su[y * SUP + colY];
+      float ax, ay;
+      ham.alpha(u.x, u.y, dmq, dpq, ax, ay);
+      if (inside) {
+        if (!isfinite(u.x + u.y + dmq + dpq)) bad = true;
+        amx = fmaxf(amx, ax);
+        amy = fmaxf(amy, ay);
+      }
+      if (p.stage == 0 || !inside) continue;
+      const float aX = local_alpha ? ax : fax, aY = local_alpha ? ay : fay;
+      const float Hv = ham.value(0.5f * (u.y + u.x), 0.5f * (dpq + dmq));
+      const float L = fmaf(aX * 0.5f, u.y - u.x, fmaf(aY * 0.5f, dpq - dmq, -Hv));
+      const int sidx = (y + 3) * SW + colY + 4;
+      const size_t g = rbase + (size_t)(gj + GY) * p.pitch + gi + GX;
+      if (PREC == P_MIXED) {
+        if (p.stage == 3) {
+          const float dd = (2.0f / 3.0f) * fmaf(dtf, L, C[sidx]);
+          float h, l;
+          df_add(A[sidx], B[sidx], dd, h, l);
+          float *oh = reinterpret_cast<float *>(p.mix_hi[i_cur ^ 1]);
+          float *ol = reinterpret_cast<float *>(p.mix_lo[i_cur ^ 1]);
+          if (edge) {
+            store_node<float, 2>(oh + rbase, p.pitch, nx, ny, d.bc, gi, gj, h);
+            store_node<float, 2>(ol + rbase, p.pitch, nx, ny, d.bc, gi, gj, l);
           } else {
-            const float dd = (p.stage == 1) ? dtf * L : 0.25f * fmaf(dtf, L, C[sidx]);
-            float *o = reinterpret_cast<float *>(p.out0);
-            if (edge) store_node<float, 2>(o + rbase, p.pitch, nx, ny, d.bc, gi, gj, dd);
-            else o[g] = dd;
+            oh[g] = h;
+            ol[g] = l;
           }
         } else {
-          const float src = A[sidx];
-          float outv;
-          if (p.stage == 1) {
-            outv = fmaf(dtf, L, src);
-          } else if (p.stage == 2) {
-            outv = fmaf(0.75f, B[sidx], 0.25f * fmaf(dtf, L, src));
-          } else {
-            outv = fmaf(1.0f / 3.0f, B[sidx], (2.0f / 3.0f) * fmaf(dtf, L, src));
-          }
+          const float dd = (p.stage == 1) ? dtf * L : 0.25f * fmaf(dtf, L, C[sidx]);
           float *o = reinterpret_cast<float *>(p.out0);
-          if (edge) store_node<float, 2>(o + rbase, p.pitch, nx, ny, d.bc, gi, gj, outv);
-          else o[g] = outv;
+          if (edge) store_node<float, 2>(o + rbase, p.pitch, nx, ny, d.bc, gi, gj, dd);
+          else o[g] = dd;
         }
-      };
-      sweep_stream<K, W>(v_at, dir == 0 ? d.rdx : d.rdy, 0.5f * (dir == 0 ? d.dx : d.dy), eps, emit);
-      if (dir == 0) __syncthreads();
+      } else {
+        const float src = A[sidx];
+        float outv;
+        if (p.stage == 1) {
+          outv = fmaf(dtf, L, src);
+        } else if (p.stage == 2) {
+          outv = fmaf(0.75f, B[sidx], 0.25f * fmaf(dtf, L, src));
+        } else {
+          outv = fmaf(1.0f / 3.0f, B[sidx], (2.0f / 3.0f) * fmaf(dtf, L, src));
+        }
+        float *o = reinterpret_cast<float *>(p.out0);
+        if (edge) store_node<float, 2>(o + rbase, p.pitch, nx, ny, d.bc, gi, gj, outv);
+        else o[g] = outv;
+      }
     }
 
     // ---- when the next tile of this CTA belongs to another instance (or there is none), fold the
