@@ -380,7 +380,9 @@ def run_ours(args):
             batched = bench_batched(args, stream)
     if not args.no_serve:
         with torch.cuda.stream(stream):
-            serving = bench_serving(args, stream, args.serve_rate)
+            rates = [float(r) for r in args.serve_rates.split(",")] if args.serve_rates else [args.serve_rate]
+            runs = [bench_serving(args, stream, r) for r in rates]
+            serving = runs[0] if len(runs) == 1 else {"sweep": runs}
 
     if rank != 0:
         return 0
@@ -459,6 +461,7 @@ def main():
     ap.add_argument("--serial-count", type=int, default=128)
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--serve-round-steps", type=int, default=4)
+    ap.add_argument("--serve-rates", type=str, default="", help="comma-separated arrival rates (a sweep)")
     ap.add_argument("--serve-count", type=int, default=120)
     ap.add_argument("--serve-budget-gb", type=float, default=60.0)
     args = ap.parse_args()

@@ -265,7 +265,9 @@ typedef struct {
  * instance of max_side x max_side.  max_slots bounds resident instances. */
 alw_status alw_server_create(const alw_scheme *scheme, size_t hbm_budget_bytes, int32_t max_slots, int32_t max_side,
                              void *cuda_stream, alw_server **out);
-/* RK3 steps each resident instance takes per round (admission granularity). */
+/* Minimum RK3 steps per round (admission granularity).  Rounds with no new
+ * instance stretch to the fewest remaining steps among the active instances,
+ * at most 16, so that a lone large solve is not slowed by round trips. */
 alw_status alw_server_set_round_steps(alw_server *s, int32_t steps);
 /* Queue a solve (host_phi0 copied); req_id receives its id. */
 alw_status alw_server_submit(alw_server *s, const alw_grid *grid, const alw_hamiltonian *ham, const double *host_phi0,

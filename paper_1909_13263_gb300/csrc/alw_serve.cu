@@ -1,12 +1,14 @@
 // Continuous-batching server for 2D HJ solves.
 //
 // Requests (grid, Hamiltonian, phi0, t_final) are queued by alw_server_submit.
-// A host worker thread runs rounds: at each round boundary it admits queued
-// requests while a slot and enough device memory are free (device-resident
-// state in one arena whose size is the memory budget), runs a few RK3 steps of
-// every resident instance together -- one persistent launch per stage over the
-// (instance, tile) work list of all of them -- and retires the instances that
-// reached their t_final (result copied to the request, memory and slot freed).
+// Two host threads share the device: a compute thread runs rounds -- a few RK3
+// steps of every active instance together, one persistent launch per stage
+// over the (instance, tile) work list of all of them -- and hands instances
+// that reached their t_final to a copier thread, which, on its own stream and
+// while rounds keep running, copies finished results out (freeing their slot
+// and rows) and admits queued requests while a slot and enough of the
+// device-memory budget are free (device-resident state in one arena whose size
+// is the budget).  New instances join at the next round boundary.
 // Requests that arrive while others are on the GPU therefore join the running
 // batch; their stages interleave in the same launches.  Every instance follows
 // the same arithmetic as a single solve, so a result does not depend on what
@@ -100,6 +102,7 @@ struct Request {
   int slot = -1;
   long long row_off = -1, rows = 0;
   int64_t steps = 0;
+  int steps_cur = 0;  // MIXED: buffer pair holding the final phi
   double t_submit = 0, t_admit = 0, t_done = 0;
 };
 
@@ -132,12 +135,15 @@ struct alw_server {
   // queue and bookkeeping
   std::mutex mu;
   std::condition_variable cv, done_cv;
-  std::deque<Request *> queue;
+  std::deque<Request *> queue;      // submitted, not yet admitted
+  std::vector<Request *> ready;     // uploaded, waiting for the next round
+  std::vector<Request *> finished;  // reached t_final, result not yet copied out
   std::map<uint64_t, Request *> reqs;
   uint64_t next_id = 1;
   bool stop = false;
   int fatal = ALW_OK;
-  std::thread worker;
+  cudaStream_t copy_stream = nullptr;  // uploads and downloads, overlapping the rounds
+  std::thread worker, copier;
   alw_server_stats stats{};
 };
 
@@ -199,8 +205,9 @@ int launch(const alw_server *s, const Stage2DParams &q) {
 
 long long rows_of(int ny) { return (long long)((ny + kTile2DY - 1) / kTile2DY) * kTile2DY + 2 * GY; }
 
-// Upload a request into its slot and rows; returns a CUDA error code (0 on success).
+// Upload a request into its slot and rows on the copy stream; returns a CUDA error code (0 on success).
 int admit_one(alw_server *s, Request *r, int slot) {
+  cudaStream_t cs = s->copy_stream;
   const int nx = r->grid.nx, ny = r->grid.ny;
   InstDesc &d = s->h_inst[slot];
   memset(&d, 0, sizeof d);
@@ -221,16 +228,14 @@ int admit_one(alw_server *s, Request *r, int slot) {
   d.ly = s->scheme.dt_mode == ALW_DT_DX53 ? std::pow(dy, 5.0 / 3.0) : dy;
   d.st = s->d_state + slot;
   const size_t n = (size_t)nx * ny;
-  memcpy(s->h_stage, r->phi0.data(), n * sizeof(double));
-  cudaError_t e = cudaMemcpyAsync(s->d_stage, s->h_stage, n * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+  cudaError_t e = cudaMemcpyAsync(s->d_stage, r->phi0.data(), n * sizeof(double), cudaMemcpyHostToDevice, cs);
   if (e != cudaSuccess) return (int)e;
   const size_t off = (size_t)r->row_off * s->pitch;
   int le;
   if (s->prec == P_MIXED)
-    le = launch_mixed_split(s->d_stage, (float *)s->arr[0] + off, (float *)s->arr[2] + off, nx, ny, s->pitch, 2,
-                            s->stream);
+    le = launch_mixed_split(s->d_stage, (float *)s->arr[0] + off, (float *)s->arr[2] + off, nx, ny, s->pitch, 2, cs);
   else
-    le = launch_unpack(s->d_stage, 0, (float *)s->arr[0] + off, 1, nx, ny, s->pitch, 2, s->stream);
+    le = launch_unpack(s->d_stage, 0, (float *)s->arr[0] + off, 1, nx, ny, s->pitch, 2, cs);
   if (le) return le;
   GhostParams g;
   memset(&g, 0, sizeof g);
@@ -247,138 +252,194 @@ int admit_one(alw_server *s, Request *r, int slot) {
   } else {
     g.a0 = (float *)s->arr[0] + off;
   }
-  le = launch_ghosts(g, s->stream);
+  le = launch_ghosts(g, cs);
   if (le) return le;
   DevState z;
   memset(&z, 0, sizeof z);
   z.t_final = r->t_final;
-  memcpy(&s->h_state[slot], &z, sizeof z);
-  e = cudaMemcpyAsync(s->d_state + slot, &s->h_state[slot], sizeof(DevState), cudaMemcpyHostToDevice, s->stream);
+  e = cudaMemcpyAsync(s->d_state + slot, &z, sizeof(DevState), cudaMemcpyHostToDevice, cs);
   if (e != cudaSuccess) return (int)e;
-  e = cudaMemcpyAsync(s->d_inst + slot, &d, sizeof(InstDesc), cudaMemcpyHostToDevice, s->stream);
+  e = cudaMemcpyAsync(s->d_inst + slot, &d, sizeof(InstDesc), cudaMemcpyHostToDevice, cs);
   if (e != cudaSuccess) return (int)e;
-  return (int)cudaStreamSynchronize(s->stream);  // staging buffers are reused
+  return (int)cudaStreamSynchronize(cs);  // the staging buffer and z are reused
 }
 
-// Copy a finished instance's phi into its request.
-int retire_one(alw_server *s, Request *r, int slot) {
+// Copy a finished instance's phi into its request on the copy stream.
+int retire_one(alw_server *s, Request *r, int slot, int cur) {
+  cudaStream_t cs = s->copy_stream;
   const InstDesc &d = s->h_inst[slot];
-  const int cur = s->h_state[slot].cur;
   const size_t n = (size_t)d.nx * d.ny, off = (size_t)d.row_off * s->pitch;
   int le;
   if (s->prec == P_MIXED)
     le = launch_mixed_join((float *)s->arr[cur] + off, (float *)s->arr[2 + cur] + off, nullptr, s->d_stage, d.nx, d.ny,
-                           s->pitch, 2, s->stream);
+                           s->pitch, 2, cs);
   else
-    le = launch_pack((float *)s->arr[0] + off, 1, s->d_stage, 0, d.nx, d.ny, s->pitch, 2, s->stream);
+    le = launch_pack((float *)s->arr[0] + off, 1, s->d_stage, 0, d.nx, d.ny, s->pitch, 2, cs);
   if (le) return le;
-  cudaError_t e = cudaMemcpyAsync(s->h_stage, s->d_stage, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-  if (e != cudaSuccess) return (int)e;
-  r->result.assign(s->h_stage, s->h_stage + n);
-  return 0;
+  r->result.resize(n);
+  cudaError_t e = cudaMemcpyAsync(r->result.data(), s->d_stage, n * sizeof(double), cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  return (int)e;
 }
 
-void worker_main(alw_server *s) {
+void set_fatal(alw_server *s, int code) {
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->fatal = ALW_ECUDA;
+  set_last_error(cudaGetErrorString((cudaError_t)code));
+  s->cv.notify_all();
+  s->done_cv.notify_all();
+}
+
+// Copier thread: retires finished instances and admits queued requests, on its own stream,
+// while the compute thread runs rounds.
+void copier_main(alw_server *s) {
   cudaSetDevice(s->device);
-  std::vector<int> list;
-  std::vector<int> new_tiles;
   for (;;) {
-    // ---- admission at a round boundary
-    std::vector<std::pair<Request *, int>> admitted;
+    std::vector<Request *> fin;
+    Request *adm = nullptr;
+    int adm_slot = -1;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      bool any_live = false;
-      for (Request *r : s->slot_req) any_live |= (r != nullptr);
-      if (!any_live && s->queue.empty())
-        s->cv.wait(lk, [&] { return s->stop || !s->queue.empty(); });
-      if (s->stop) return;
-      while (!s->queue.empty()) {
-        Request *r = s->queue.front();
-        int slot = -1;
+      auto can_admit = [&]() -> bool {
+        if (s->queue.empty()) return false;
         for (int i = 0; i < s->max_slots; ++i)
-          if (!s->slot_req[i]) {
-            slot = i;
-            break;
-          }
-        if (slot < 0) break;
+          if (!s->slot_req[i]) return true;
+        return false;
+      };
+      s->cv.wait(lk, [&] { return s->stop || s->fatal || !s->finished.empty() || can_admit(); });
+      if (s->stop || s->fatal) return;
+      fin.swap(s->finished);
+      if (fin.empty() && can_admit()) {
+        Request *r = s->queue.front();
         const long long need = rows_of(r->grid.ny);
         const long long at = s->rows.take(need);
-        if (at < 0) break;  // wait for memory: FIFO, no overtaking
-        s->queue.pop_front();
-        r->slot = slot;
-        r->row_off = at;
-        r->rows = need;
-        r->t_admit = now_s();
-        s->slot_req[slot] = r;
-        s->stats.admitted++;
-        admitted.emplace_back(r, slot);
+        if (at >= 0) {  // FIFO: otherwise wait for a retirement to free rows
+          int slot = 0;
+          while (s->slot_req[slot]) ++slot;
+          s->queue.pop_front();
+          r->slot = slot;
+          r->row_off = at;
+          r->rows = need;
+          r->t_admit = now_s();
+          s->slot_req[slot] = r;
+          s->stats.admitted++;
+          adm = r;
+          adm_slot = slot;
+        } else if (s->finished.empty()) {
+          // nothing to retire and no room: wait for the compute thread to finish an instance
+          s->cv.wait(lk, [&] { return s->stop || s->fatal || !s->finished.empty(); });
+          continue;
+        }
       }
       s->stats.queued = (int64_t)s->queue.size();
     }
-    for (auto &ar : admitted) {
-      const int e = admit_one(s, ar.first, ar.second);
-      if (e) {
-        std::lock_guard<std::mutex> lk(s->mu);
-        s->fatal = ALW_ECUDA;
-        set_last_error(cudaGetErrorString((cudaError_t)e));
-        s->done_cv.notify_all();
+    for (Request *r : fin) {
+      const int re = r->status == ALW_OK ? retire_one(s, r, r->slot, r->steps_cur) : 0;
+      if (re) {
+        set_fatal(s, re);
         return;
       }
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (r->status == ALW_OK) r->status = ALW_OK;
+      r->t_done = now_s();
+      r->done = 1;
+      s->rows.give(r->row_off, r->rows);
+      s->slot_req[r->slot] = nullptr;
+      s->stats.completed++;
+      s->done_cv.notify_all();
+      s->cv.notify_all();
     }
-    // ---- work list of every resident instance (new ones primed first)
+    if (adm) {
+      const int e = admit_one(s, adm, adm_slot);
+      if (e) {
+        set_fatal(s, e);
+        return;
+      }
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->ready.push_back(adm);
+      s->cv.notify_all();
+    }
+  }
+}
+
+// Compute thread: rounds of RK steps over every active instance.
+void worker_main(alw_server *s) {
+  cudaSetDevice(s->device);
+  std::vector<int> list, new_tiles;
+  std::vector<Request *> active;
+  for (;;) {
+    std::vector<Request *> fresh;
+    int steps = 1;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv.wait(lk, [&] { return s->stop || s->fatal || !active.empty() || !s->ready.empty(); });
+      if (s->stop || s->fatal) return;
+      fresh.swap(s->ready);
+      steps = s->steps_per_round;
+    }
+    for (Request *r : fresh) active.push_back(r);
+    // round length: long enough to amortise the round trip, short enough that the first
+    // active instance to finish is retired promptly (its remaining steps, at most 16)
+    if (fresh.empty()) {
+      double rem_min = 1e30;
+      for (Request *r : active) {
+        const DevState &ds = s->h_state[r->slot];
+        if (ds.dt > 0.0) rem_min = std::min(rem_min, std::ceil((ds.t_final - ds.t) / ds.dt));
+      }
+      if (rem_min < 1e29) steps = std::max(steps, std::min(16, (int)rem_min));
+    }
     list.clear();
     new_tiles.clear();
-    for (int i = 0; i < s->max_slots; ++i) {
-      Request *r = s->slot_req[i];
-      if (!r) continue;
-      bool is_new = false;
-      for (auto &ar : admitted) is_new |= (ar.second == i);
-      for (int t = 0; t < s->h_inst[i].ntiles; ++t) {
-        list.push_back(i * 65536 + t);
-        if (is_new) new_tiles.push_back(i * 65536 + t);
+    for (Request *r : active) {
+      const bool is_new = std::find(fresh.begin(), fresh.end(), r) != fresh.end();
+      for (int t = 0; t < s->h_inst[r->slot].ntiles; ++t) {
+        list.push_back(r->slot * 65536 + t);
+        if (is_new) new_tiles.push_back(r->slot * 65536 + t);
       }
     }
-    if (list.empty()) continue;
     cudaError_t e = cudaSuccess;
     int le = 0;
-    if (!new_tiles.empty()) {
+    if (!new_tiles.empty()) {  // first lagged alpha of the new instances
       e = cudaMemcpyAsync(s->d_tiles, new_tiles.data(), new_tiles.size() * sizeof(int), cudaMemcpyHostToDevice,
                           s->stream);
       if (e == cudaSuccess) le = launch(s, server_params(s, 0, LOOP_ADVANCE, (int)new_tiles.size()));
-      if (e == cudaSuccess && !le) e = cudaStreamSynchronize(s->stream);
     }
     if (e == cudaSuccess && !le)
-      e = cudaMemcpyAsync(s->d_tiles, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice, s->stream);
-    for (int k = 0; k < s->steps_per_round && e == cudaSuccess && !le; ++k)
-      for (int stage = 1; stage <= 3 && !le; ++stage) le = launch(s, server_params(s, stage, LOOP_STEP_TO, (int)list.size()));
+      e = cudaMemcpyAsync(s->d_tiles + new_tiles.size(), list.data(), list.size() * sizeof(int),
+                          cudaMemcpyHostToDevice, s->stream);
+    Stage2DParams q;
+    for (int k = 0; k < steps && e == cudaSuccess && !le; ++k)
+      for (int stage = 1; stage <= 3 && !le; ++stage) {
+        q = server_params(s, stage, LOOP_STEP_TO, (int)list.size());
+        q.tiles = s->d_tiles + new_tiles.size();
+        le = launch(s, q);
+      }
     if (e == cudaSuccess && !le)
       e = cudaMemcpyAsync(s->h_state, s->d_state, sizeof(DevState) * s->max_slots, cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess && !le) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess || le) {
-      std::lock_guard<std::mutex> lk(s->mu);
-      s->fatal = ALW_ECUDA;
-      set_last_error(cudaGetErrorString(e != cudaSuccess ? e : (cudaError_t)le));
-      s->done_cv.notify_all();
+      set_fatal(s, e != cudaSuccess ? (int)e : le);
       return;
     }
+    // instances that reached t_final (or failed) leave the active set for the copier
+    std::vector<Request *> keep, done;
+    for (Request *r : active) {
+      const DevState &ds = s->h_state[r->slot];
+      if (ds.t < ds.t_final && !ds.err) {
+        keep.push_back(r);
+      } else {
+        r->status = ds.err ? ALW_ENONFINITE : ALW_OK;
+        r->steps = ds.steps;
+        r->steps_cur = ds.cur;
+        done.push_back(r);
+      }
+    }
+    active.swap(keep);
+    std::lock_guard<std::mutex> lk(s->mu);
     s->stats.rounds++;
-    // ---- retire finished instances
-    for (int i = 0; i < s->max_slots; ++i) {
-      Request *r = s->slot_req[i];
-      if (!r) continue;
-      const DevState &ds = s->h_state[i];
-      if (ds.t < ds.t_final && !ds.err) continue;
-      const int re = ds.err ? 0 : retire_one(s, r, i);
-      std::lock_guard<std::mutex> lk(s->mu);
-      r->status = ds.err ? ALW_ENONFINITE : (re ? ALW_ECUDA : ALW_OK);
-      r->steps = ds.steps;
-      r->t_done = now_s();
-      r->done = 1;
-      s->rows.give(r->row_off, r->rows);
-      s->slot_req[i] = nullptr;
-      s->stats.completed++;
-      s->done_cv.notify_all();
+    if (!done.empty()) {
+      for (Request *r : done) s->finished.push_back(r);
+      s->cv.notify_all();
     }
   }
 }
@@ -451,7 +512,7 @@ alw_status alw_server_create(const alw_scheme *scheme, size_t hbm_budget_bytes, 
     if (p) s->allocs.emplace_back(p, bytes);
     return p;
   };
-  s->tiles_cap = max_slots * tiles_max;
+  s->tiles_cap = 2 * max_slots * tiles_max;  // new instances' tiles, then the whole work list
   s->d_inst = (InstDesc *)grab(sizeof(InstDesc) * max_slots);
   s->d_state = (DevState *)grab(sizeof(DevState) * max_slots);
   s->d_tiles = (int *)grab(sizeof(int) * (size_t)s->tiles_cap);
@@ -470,7 +531,10 @@ alw_status alw_server_create(const alw_scheme *scheme, size_t hbm_budget_bytes, 
   s->h_inst.assign(max_slots, InstDesc{});
   s->slot_req.assign(max_slots, nullptr);
   s->stats.arena_rows = s->rows_total;
+  if (cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail_destroy(serr(ALW_ECUDA, "stream creation failed"));
   s->worker = std::thread(worker_main, s);
+  s->copier = std::thread(copier_main, s);
   *out = s;
   return ALW_OK;
 }
@@ -564,7 +628,12 @@ alw_status alw_server_destroy(alw_server *s) {
     s->cv.notify_all();
   }
   if (s->worker.joinable()) s->worker.join();
+  if (s->copier.joinable()) s->copier.join();
   cudaStreamSynchronize(s->stream);
+  if (s->copy_stream) {
+    cudaStreamSynchronize(s->copy_stream);
+    cudaStreamDestroy(s->copy_stream);
+  }
   for (auto &a : s->allocs) dev_free(a.first, a.second, s->stream);
   cudaStreamSynchronize(s->stream);
   if (s->h_state) cudaFreeHost(s->h_state);
