@@ -441,6 +441,80 @@ def run_ours(args):
     return 0
 
 
+def run_precision_report(args):
+    """Errors of the float paths against FP64 and against the exact solution (one JSON line).
+
+    Example 3 (periodic, exact solution by characteristics) on 400^2 and 2048^2 to t = 0.5/pi^2:
+    L1 (mean |e|) and max |e| of FP64, MIXED and FP32 against the exact solution, and of MIXED and
+    FP32 against FP64.  Example 10 (sin(p+q), pi(|y|-|x|), linear extrapolation) on 1024^2 to t = 1:
+    MIXED and FP32 against FP64 (no exact solution).  Plus FP64 throughput at 2048^2."""
+    import numpy as np
+    import torch
+
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import exact
+    from paper_1909_13263_gb300 import inputs, native
+
+    native.load()
+    native.use_torch_allocator(True)
+    out = {"report": "precision"}
+    tf = 0.5 / math.pi**2
+    for n in (400, 2048):
+        x, dx = inputs.axis(n, -2.0, 2.0, "periodic")
+        phi0 = inputs.phi0_negcos_diag_2d(x, x)
+        ex = exact.negcos_diag_2d("burgers2d", x, x, tf)
+        res = {}
+        for prec in ("fp64", "mixed", "fp32"):
+            with native.Solver(dim=2, nx=n, ny=n, xlo=-2.0, xhi=2.0, ylo=-2.0, yhi=2.0, ham="burgers2d",
+                               precision=prec) as s:
+                s.set_phi0(phi0)
+                s.step_to(tf)
+                res[prec] = s.get_phi()
+        row = {}
+        for prec, phi in res.items():
+            e = np.abs(phi - ex)
+            row[prec] = {"l1_vs_exact": float(e.mean()), "linf_vs_exact": float(e.max())}
+            if prec != "fp64":
+                d = np.abs(phi - res["fp64"])
+                row[prec].update({"l1_vs_fp64": float(d.mean()), "linf_vs_fp64": float(d.max()),
+                                  "l1_ratio_to_fp64": float(e.mean() / np.abs(res["fp64"] - ex).mean())})
+        out[f"ex3_burgers2d_{n}sq"] = row
+    n = 1024
+    x, dx = inputs.axis(n, -1.0, 1.0, "linextrap")
+    phi0 = inputs.phi0_riemann_2d(x, x)
+    res = {}
+    for prec in ("fp64", "mixed", "fp32"):
+        with native.Solver(dim=2, nx=n, ny=n, bc="linextrap", xlo=-1.0, xhi=1.0, ylo=-1.0, yhi=1.0, ham="sin2d",
+                           precision=prec) as s:
+            s.set_phi0(phi0)
+            steps = s.step_to(1.0)
+            res[prec] = s.get_phi()
+    row = {"steps": steps}
+    for prec in ("mixed", "fp32"):
+        d = np.abs(res[prec] - res["fp64"])
+        row[prec] = {"l1_vs_fp64": float(d.mean()), "linf_vs_fp64": float(d.max())}
+    out[f"ex10_sin2d_linextrap_{n}sq"] = row
+    # FP64 throughput (the parity path): RK3 steps of Example 3 on 2048^2
+    n = 2048
+    x, dx = inputs.axis(n, -2.0, 2.0, "periodic")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        with native.Solver(dim=2, nx=n, ny=n, xlo=-2.0, xhi=2.0, ylo=-2.0, yhi=2.0, ham="burgers2d",
+                           precision="fp64", stream=stream) as s:
+            s.set_phi0(inputs.phi0_negcos_diag_2d(x, x))
+            s.advance(3)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.advance(10)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 10
+    out["fp64_ex3_2048sq"] = {"ms_per_step": ms, "point_updates_per_s": n * n / (ms * 1e-3)}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -462,6 +536,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--serve-round-steps", type=int, default=4)
     ap.add_argument("--serve-rates", type=str, default="", help="comma-separated arrival rates (a sweep)")
+    ap.add_argument("--report", choices=["", "precision"], default="",
+                    help="precision: errors of the float paths against FP64 and the exact solution")
     ap.add_argument("--serve-count", type=int, default=120)
     ap.add_argument("--serve-budget-gb", type=float, default=60.0)
     args = ap.parse_args()
@@ -469,6 +545,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.report == "precision":
+        return run_precision_report(args)
     return run_ours(args)
 
 
