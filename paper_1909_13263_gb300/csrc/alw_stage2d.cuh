@@ -340,15 +340,15 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
       const float2 u = su[y * SUP + colY];
       float ax, ay;
       ham.alpha(u.x, u.y, dmq, dpq, ax, ay);
+      const float aX = local_alpha ? ax : fax, aY = local_alpha ? ay : fay;
+      const float Hv = ham.value(0.5f * (u.y + u.x), 0.5f * (dpq + dmq));
+      const float L = fmaf(aX * 0.5f, u.y - u.x, fmaf(aY * 0.5f, dpq - dmq, -Hv));
       if (inside) {
-        if (!isfinite(u.x + u.y + dmq + dpq)) bad = true;
+        if (!isfinite(L)) bad = true;   // L depends on all four one-sided derivatives
         amx = fmaxf(amx, ax);
         amy = fmaxf(amy, ay);
       }
       if (p.stage == 0 || !inside) continue;
-      const float aX = local_alpha ? ax : fax, aY = local_alpha ? ay : fay;
-      const float Hv = ham.value(0.5f * (u.y + u.x), 0.5f * (dpq + dmq));
-      const float L = fmaf(aX * 0.5f, u.y - u.x, fmaf(aY * 0.5f, dpq - dmq, -Hv));
       const int sidx = (y + 3) * SW + colY + 4;
       const size_t g = rbase + (size_t)(gj + GY) * p.pitch + gi + GX;
       if (PREC == P_MIXED) {

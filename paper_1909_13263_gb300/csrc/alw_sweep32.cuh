@@ -64,12 +64,10 @@ __device__ __forceinline__ FValV<V> f_eval_v(V u) {
 #pragma unroll
   for (int i = 0; i < LN::n; ++i) LN::at(rs, i) = rsqrtf(LN::get(t, i));
   r.s = vmul(t, rs);
-  V au;
+  // |u| + s per lane (the absolute value is an operand modifier of the scalar add)
 #pragma unroll
-  for (int i = 0; i < LN::n; ++i) LN::at(au, i) = fabsf(LN::get(u, i));
-  const V arg = vadd(au, r.s);
-#pragma unroll
-  for (int i = 0; i < LN::n; ++i) LN::at(lsg, i) = copysignf(__log2f(LN::get(arg, i)), LN::get(u, i));
+  for (int i = 0; i < LN::n; ++i)
+    LN::at(lsg, i) = copysignf(__log2f(fabsf(LN::get(u, i)) + LN::get(r.s, i)), LN::get(u, i));
   // asinh|u| = ln(|u| + sqrt(1+u^2)); absolute error of the base-2 log ~ 2^-22
   r.F = vfma(vsplat(0.693147180559945f, u), lsg, vmul(u, r.s));
   return r;
@@ -83,12 +81,15 @@ __device__ __forceinline__ V q_interval_v(V a, FValV<V> fa, V b, FValV<V> fb, V 
   const V ss = vadd(fa.s, fb.s);          // trapezoid value of G2
   const V dF = vsub(fb.F, fa.F);
   const V thr = vmul(vsplat(0.015625f, h), ss);
+  V rh;
+#pragma unroll
+  for (int i = 0; i < LN::n; ++i) LN::at(rh, i) = __fdividef(1.0f, LN::get(h, i));
+  const V gd = vmul(dF, rh);
   V g;
 #pragma unroll
   for (int i = 0; i < LN::n; ++i) {
-    const float hi = LN::get(h, i);
     // divided difference, or the trapezoid mean when the interval is short compared with its ends
-    LN::at(g, i) = (fabsf(hi) > LN::get(thr, i)) ? __fdividef(LN::get(dF, i), hi) : LN::get(ss, i);
+    LN::at(g, i) = (fabsf(LN::get(h, i)) > LN::get(thr, i)) ? LN::get(gd, i) : LN::get(ss, i);
   }
   const V e = vfma(g, g, eps4);
   return vmul(e, e);
@@ -109,19 +110,22 @@ __device__ __forceinline__ V side_corr_v(V q0, V q1, V q2, V ta3, V tb2) {
   const V A0 = vmul(q1, q2), A1 = vmul(q0, q2), A2 = vmul(q0, q1);
   const V den = vfma(vsplat(6.0f, q0), A1, vfma(vsplat(3.0f, q0), A2, A0));
   const V num = vfma(A0, ta3, vmul(A2, tb2));
-  V out;
+  // den >= A0 > 0 cannot underflow (arc length: q >= 16; Jiang-Peng: q >= eps^2), so only the
+  // upper end of the float range needs a check (NaN fails it too)
+  V rd;
   bool ok = true;
 #pragma unroll
   for (int i = 0; i < LN::n; ++i) {
     const float dn = LN::get(den, i);
-    ok = ok && (dn > 1e-30f && dn < 1e30f);
-    LN::at(out, i) = __fdividef(LN::get(num, i), dn);
+    ok = ok && (dn < 1e30f);
+    LN::at(rd, i) = __fdividef(1.0f, dn);
   }
+  V out = vmul(num, rd);
   if (!ok) {
 #pragma unroll
     for (int i = 0; i < LN::n; ++i) {
       const float dn = LN::get(den, i);
-      if (!(dn > 1e-30f && dn < 1e30f))
+      if (!(dn < 1e30f))
         LN::at(out, i) = side_corr_wide(LN::get(q0, i), LN::get(q1, i), LN::get(q2, i), LN::get(ta3, i),
                                         LN::get(tb2, i));
     }
