@@ -26,7 +26,7 @@ _lock = threading.Lock()
 _lib = None
 
 HAM = {"burgers2d": 0, "negcos2d": 1, "sin2d": 2, "advect1d": 3, "burgers1d": 4,
-       "negcos1d": 5, "eikonal2d": 6}
+       "negcos1d": 5, "eikonal2d": 6, "nonconvex1d": 7}
 BC = {"periodic": 0, "linextrap": 1}
 WEIGHTS = {"arclength": 0, "jp": 1}
 ALPHA = {"local_lagged": 0, "local_exact": 1, "global_lagged": 2, "global_exact": 3, "fixed": 4}
@@ -94,6 +94,8 @@ def lib():
         L.orc_rk3_step_generic.argtypes = [ctypes.c_int64, dp, ctypes.c_double, L_FN, ctypes.c_void_p]
         L.orc_point_L.restype = ctypes.c_double
         L.orc_point_L.argtypes = [cp, dp, ctypes.c_int, ctypes.c_int, dp]
+        L.orc_node_alpha.restype = None
+        L.orc_node_alpha.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 + [dp]
         _lib = L
     return _lib
 
@@ -150,6 +152,13 @@ def ham(kind: str, p: float, q: float = 0.0):
     if st:
         raise ValueError(kind)
     return H.value, Hp.value, Hq.value
+
+
+def node_alpha(kind: str, dim: int, um, up, vm=0.0, vp=0.0):
+    """The node-local Lax-Friedrichs alpha pair (alpha_x, alpha_y)."""
+    out = np.zeros(2)
+    lib().orc_node_alpha(HAM[kind], dim, um, up, vm, vp, _dp(out))
+    return out
 
 
 def hhat(kind: str, up, um, vp=0.0, vm=0.0, ax=0.0, ay=0.0) -> float:

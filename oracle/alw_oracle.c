@@ -25,7 +25,9 @@
  *       is 0/0 there); c == 0 uses the printed c = 0 branch.
  *   R5  alpha of the Lax-Friedrichs flux ("max over u of |H_1(u)|", range
  *       unstated): by default the node's own maximum of |dH/dp| (|dH/dq|)
- *       over the four combinations (u^-/u^+, v^-/v^+) -- the local form,
+ *       over the four combinations (u^-/u^+, v^-/v^+) -- the local form
+ *       (for the non-convex H of Example 8, whose H_p is not monotone, the
+ *       maximum over the whole interval between u^- and u^+),
  *       which reproduces Table 2; the grid-wide maximum of the same values
  *       (global form) and fixed constants are the other modes.  The time
  *       step always uses a grid-wide maximum: of the previous stage
@@ -57,7 +59,8 @@ enum {
   ORC_H_ADVECT1D = 3,  /* p                 Example 1 */
   ORC_H_BURGERS1D = 4, /* (p+1)^2/2         Example 6 */
   ORC_H_NEGCOS1D = 5,  /* -cos(p+1)         Example 2 */
-  ORC_H_EIKONAL2D = 6  /* sqrt(p^2+q^2+1)   Example 12 */
+  ORC_H_EIKONAL2D = 6, /* sqrt(p^2+q^2+1)   Example 12 */
+  ORC_H_NONCONVEX1D = 7 /* (p^2-1)(p^2-4)/4 Example 8 */
 };
 enum {
   ORC_ALPHA_LOCAL_LAGGED = 0,  /* flux: per-node alpha; dt: previous stage's grid max */
@@ -197,6 +200,8 @@ int orc_ham(int kind, double p, double q, double *H, double *Hp, double *Hq) {
       const double r = sqrt(p * p + q * q + 1.0);
       h = r; hp = p / r; hq = q / r;
     } break;
+    case ORC_H_NONCONVEX1D:
+      h = 0.25 * (p * p - 1.0) * (p * p - 4.0); hp = p * p * p - 2.5 * p; hq = 0.0; break;
     default: return ORC_EINVAL;
   }
   if (H) *H = h;
@@ -260,34 +265,27 @@ void orc_derivs(const orc_cfg *cfg, const double *phi, double *um, double *up, d
     }
 }
 
-/* Reading R5: alpha_x = max |H_p|, alpha_y = max |H_q| over nodes and the four
- * (u, v) combinations.  Returns ORC_ENONFINITE if a value is not finite. */
-int orc_alpha_max(const orc_cfg *cfg, const double *um, const double *up, const double *vm,
-                  const double *vp, double out[2]) {
-  double ax = 0.0, ay = 0.0;
-  int bad = 0;
-  const ptrdiff_t n = (ptrdiff_t)cfg->nx * cfg->ny;
-  for (ptrdiff_t k = 0; k < n; ++k) {
-    const double us[2] = {um[k], up[k]}, vs[2] = {vm[k], vp[k]};
-    for (int a = 0; a < 2; ++a)
-      for (int b = 0; b < 2; ++b) {
-        double hp, hq;
-        orc_ham(cfg->ham, us[a], vs[b], NULL, &hp, &hq);
-        if (!isfinite(hp) || !isfinite(hq)) bad = 1;
-        if (fabs(hp) > ax) ax = fabs(hp);
-        if (fabs(hq) > ay) ay = fabs(hq);
-      }
-  }
-  out[0] = ax;
-  out[1] = (cfg->dim == 2) ? ay : 0.0;
-  return bad ? ORC_ENONFINITE : ORC_OK;
-}
-
 /* Reading R5, local form: the node's own alpha = max over the four (u, v)
  * combinations at that node of |H_p| (resp. |H_q|). */
-static void node_alpha(int ham, int dim, double um, double up, double vm, double vp, double out[2]) {
+void orc_node_alpha(int ham, int dim, double um, double up, double vm, double vp, double out[2]) {
   const double us[2] = {um, up}, vs[2] = {vm, vp};
   double ax = 0.0, ay = 0.0;
+  if (ham == ORC_H_NONCONVEX1D) {
+    /* H_p = p^3 - 5p/2 is not monotone: its largest modulus on [min(u), max(u)] is at an end or
+       where H_pp = 3p^2 - 5/2 vanishes, p = +-sqrt(5/6) */
+    const double lo = fmin(um, up), hi = fmax(um, up), c = sqrt(5.0 / 6.0);
+    const double cand[4] = {lo, hi, -c, c};
+    for (int k = 0; k < 4; ++k) {
+      if (k >= 2 && !(cand[k] > lo && cand[k] < hi)) continue;
+      double hp;
+      orc_ham(ham, cand[k], 0.0, NULL, &hp, NULL);
+      if (fabs(hp) > ax || isnan(hp)) ax = fabs(hp);
+    }
+    if (isnan(um) || isnan(up)) ax = NAN;
+    out[0] = ax;
+    out[1] = 0.0;
+    return;
+  }
   for (int a = 0; a < 2; ++a)
     for (int b = 0; b < 2; ++b) {
       double hp, hq;
@@ -299,6 +297,25 @@ static void node_alpha(int ham, int dim, double um, double up, double vm, double
   out[1] = (dim == 2) ? ay : 0.0;
 }
 
+/* Reading R5: alpha_x = max |H_p|, alpha_y = max |H_q| over nodes and the four
+ * (u, v) combinations.  Returns ORC_ENONFINITE if a value is not finite. */
+int orc_alpha_max(const orc_cfg *cfg, const double *um, const double *up, const double *vm,
+                  const double *vp, double out[2]) {
+  double ax = 0.0, ay = 0.0;
+  int bad = 0;
+  const ptrdiff_t n = (ptrdiff_t)cfg->nx * cfg->ny;
+  for (ptrdiff_t k = 0; k < n; ++k) {
+    double a[2];
+    orc_node_alpha(cfg->ham, cfg->dim, um[k], up[k], vm[k], vp[k], a);
+    if (!isfinite(a[0]) || !isfinite(a[1])) bad = 1;
+    if (a[0] > ax) ax = a[0];
+    if (a[1] > ay) ay = a[1];
+  }
+  out[0] = ax;
+  out[1] = (cfg->dim == 2) ? ay : 0.0;
+  return bad ? ORC_ENONFINITE : ORC_OK;
+}
+
 /* Eq. SDE: L(phi) = -Hhat at every node.  alpha_mode selects the alpha of the
  * Lax-Friedrichs flux: per node (LOCAL_*), or the given grid-wide pair. */
 void orc_L_from_derivs(const orc_cfg *cfg, const double *um, const double *up, const double *vm,
@@ -307,7 +324,7 @@ void orc_L_from_derivs(const orc_cfg *cfg, const double *um, const double *up, c
   const int local = (cfg->alpha_mode == ORC_ALPHA_LOCAL_LAGGED || cfg->alpha_mode == ORC_ALPHA_LOCAL_EXACT);
   for (ptrdiff_t k = 0; k < n; ++k) {
     double a[2] = {alpha[0], alpha[1]};
-    if (local) node_alpha(cfg->ham, cfg->dim, um[k], up[k], vm[k], vp[k], a);
+    if (local) orc_node_alpha(cfg->ham, cfg->dim, um[k], up[k], vm[k], vp[k], a);
     L[k] = -orc_hhat(cfg->ham, up[k], um[k], vp[k], vm[k], a[0], cfg->dim == 2 ? a[1] : 0.0);
   }
 }
@@ -451,6 +468,6 @@ double orc_point_L(const orc_cfg *cfg, const double *phi, int i, int j, const do
   double d[4], a[2] = {alpha[0], alpha[1]};
   orc_point_derivs(cfg, phi, i, j, d);
   if (cfg->alpha_mode == ORC_ALPHA_LOCAL_LAGGED || cfg->alpha_mode == ORC_ALPHA_LOCAL_EXACT)
-    node_alpha(cfg->ham, cfg->dim, d[0], d[1], d[2], d[3], a);
+    orc_node_alpha(cfg->ham, cfg->dim, d[0], d[1], d[2], d[3], a);
   return -orc_hhat(cfg->ham, d[1], d[0], d[3], d[2], a[0], cfg->dim == 2 ? a[1] : 0.0);
 }

@@ -54,6 +54,27 @@ def phi0_eikonal_2d(x, y):
     return 0.25 * (np.cos(2 * np.pi * X) - 1.0) * (np.cos(2 * np.pi * Y) - 1.0) - 1.0
 
 
+def phi0_corners_1d(x):
+    """Example 5: phi(x, 0) = f(x - 0.5), f a linear ramp plus four smooth pieces meeting at
+    corners (x = -1/3, 0, 1/3), extended periodically from [-1, 1).
+
+    The third piece is taken as 15/2 - 3 cos(2 pi x): the printed constant 5/2 would leave
+    jumps of 5 at x = 0 and x = 1/3, whereas 15/2 makes f continuous there and periodic."""
+    z = np.asarray(x, dtype=np.float64) - 0.5
+    z = (z + 1.0) % 2.0 - 1.0
+    base = -(np.sqrt(3.0) / 2.0 + 4.5 + 2.0 * np.pi / 3.0) * (z + 1.0)
+    out = np.where(z < -1.0 / 3.0, 2.0 * np.cos(1.5 * np.pi * z * z) - np.sqrt(3.0),
+          np.where(z < 0.0, 1.5 + 3.0 * np.cos(2.0 * np.pi * z),
+          np.where(z < 1.0 / 3.0, 7.5 - 3.0 * np.cos(2.0 * np.pi * z),
+                   (28.0 + 4.0 * np.pi + np.cos(3.0 * np.pi * z)) / 3.0 + 6.0 * np.pi * z * (z - 1.0))))
+    return base + out
+
+
+def phi0_abs_1d(x):
+    """Example 8: phi(x, 0) = -2|x|."""
+    return -2.0 * np.abs(np.asarray(x, dtype=np.float64))
+
+
 def random_field(ny: int, nx: int, seed: int, kind: str = "smooth") -> np.ndarray:
     """Seeded test data: 'smooth' (few Fourier modes), 'rough' (smooth + kinks + noise)."""
     rng = np.random.default_rng(seed)
@@ -95,6 +116,8 @@ PROBLEMS = {
     "ex4_negcos2d": Problem("ex4_negcos2d", 2, "negcos2d", -2.0, 2.0, "periodic", 0.5 / math.pi**2, "negcos_diag"),
     "ex10_sin2d": Problem("ex10_sin2d", 2, "sin2d", -1.0, 1.0, "linextrap", 1.0, "riemann"),
     "ex12_eikonal2d": Problem("ex12_eikonal2d", 2, "eikonal2d", 0.0, 1.0, "periodic", 0.6, "eikonal"),
+    "ex5_corners": Problem("ex5_corners", 1, "advect1d", -1.0, 1.0, "periodic", 2.0, "corners"),
+    "ex8_nonconvex1d": Problem("ex8_nonconvex1d", 1, "nonconvex1d", -1.0, 1.0, "periodic", 1.0, "abs"),
 }
 
 
@@ -102,9 +125,8 @@ def initial(problem: Problem, n: int, theta: float = 0.0):
     """(phi0, dx) for a problem on an n-node (or n x n) grid."""
     x, dx = axis(n, problem.lo, problem.hi, problem.bc)
     if problem.dim == 1:
-        if problem.phi0 != "negcos1d":
-            raise ValueError(problem.phi0)
-        return phi0_negcos_1d(x), dx
+        f = {"negcos1d": phi0_negcos_1d, "corners": phi0_corners_1d, "abs": phi0_abs_1d}[problem.phi0]
+        return f(x), dx
     if problem.phi0 == "negcos_diag":
         return phi0_negcos_diag_2d(x, x, theta), dx
     if problem.phi0 == "riemann":

@@ -114,3 +114,63 @@ def test_burgers_1d_kink_is_non_oscillatory(weights):
     assert phi.max() <= 1.0 + 1e-12
     d2 = np.diff(phi, 2)
     assert np.sum(np.abs(np.diff(np.sign(d2[np.abs(d2) > 1e-3]))) > 0) <= 6
+
+
+def test_example5_initial_data_is_continuous_and_periodic():
+    # the third piece read as 15/2 - 3cos(2 pi x): continuous at the corners, periodic on [-1, 1)
+    f = inputs.phi0_corners_1d
+    for c in (0.5 - 1.0 / 3.0, 0.5, 0.5 + 1.0 / 3.0, -0.5):
+        assert abs(f(c - 1e-12) - f(c)) < 1e-9
+    assert abs(f(-1.0) - f(1.0 - 1e-13)) < 1e-9
+    # corners: one-sided slopes differ at x - 0.5 = -1/3 and 1/3, agree at 0
+    h = 1e-7
+    slope = lambda c: ((f(c + h) - f(c)) / h, (f(c) - f(c - h)) / h)
+    for c, corner in ((0.5 - 1.0 / 3.0, True), (0.5, False), (0.5 + 1.0 / 3.0, True)):
+        r, l = slope(c)
+        assert (abs(r - l) > 1.0) == corner
+
+
+@pytest.mark.parametrize("t_final", [2.0, 8.0])
+def test_example5_arclength_sharper_at_corners(t_final):
+    # Example 5 (N = 100, CFL 0.6): the exact solution is phi0(x - t); near each corner of
+    # the profile the arc-length weights give a smaller error than the Jiang-Peng weights
+    n = 100
+    x, dx = inputs.axis(n, -1.0, 1.0, "periodic")
+    ex = inputs.phi0_corners_1d(x - t_final)
+    err = {}
+    for w in ("arclength", "jp"):
+        cfg = oracle.make_cfg(dim=1, nx=n, dx=dx, ham="advect1d", weights=w, alpha_mode="local_lagged")
+        phi, _, t, _, st = oracle.solve(cfg, inputs.phi0_corners_1d(x), t_final)
+        assert st == 0 and t == t_final
+        err[w] = np.abs(phi - ex)
+    for c in (0.5 - 1.0 / 3.0, 0.5 + 1.0 / 3.0, -0.5):
+        near = np.abs(((x - c + 1.0) % 2.0) - 1.0) < 0.1
+        assert err["arclength"][near].max() < err["jp"][near].max()
+    assert err["arclength"].max() < 1.0
+
+
+def _hopf_example8(x, t):
+    # phi0 = -2|x| is concave: psi = -phi has convex data 2|x| whose conjugate is 0 on [-2, 2],
+    # so Hopf's formula gives phi(x, t) = -max_{|q| <= 2} (x q + t H(q)) on the whole line
+    q = np.linspace(-2.0, 2.0, 200001)
+    hq = 0.25 * (q * q - 1.0) * (q * q - 4.0)
+    return np.array([-np.max(xi * q + t * hq) for xi in x])
+
+
+@pytest.mark.parametrize("weights", ["arclength", "jp"])
+def test_example8_nonconvex_matches_hopf_formula(weights):
+    # Example 8 on the periodic grid up to t = 0.15: with |H_p| <= 3 on [-2, 2] the corners of
+    # the periodic profile at x = +-1 do not reach |x| <= 0.4, where Hopf's formula holds
+    tf = 0.15
+    l1 = []
+    for n in (100, 200, 400):
+        x, dx = inputs.axis(n, -1.0, 1.0, "periodic")
+        cfg = oracle.make_cfg(dim=1, nx=n, dx=dx, ham="nonconvex1d", weights=weights, alpha_mode="local_lagged")
+        phi, _, t, _, st = oracle.solve(cfg, inputs.phi0_abs_1d(x), tf)
+        assert st == 0 and t == tf
+        near = np.abs(x) <= 0.4
+        e = np.abs(phi - _hopf_example8(x, tf))[near]
+        l1.append(dx * e.sum())
+        if n == 400:
+            assert e.max() < 5e-3
+    assert l1[0] / l1[1] > 1.7 and l1[1] / l1[2] > 1.7, l1

@@ -227,6 +227,7 @@ HAMS2 = {
     "advect1d": (lambda p, q: p),
     "burgers1d": (lambda p, q: 0.5 * (p + 1) ** 2),
     "negcos1d": (lambda p, q: -np.cos(p + 1)),
+    "nonconvex1d": (lambda p, q: 0.25 * (p * p - 1) * (p * p - 4)),
 }
 
 
@@ -324,3 +325,19 @@ def test_mirror_and_transpose_symmetry():
     b = oracle.derivs(ct, ph2.T.copy())
     np.testing.assert_array_equal(a[0], b[2].T)
     np.testing.assert_array_equal(a[1], b[3].T)
+
+
+def test_nonconvex_alpha_is_the_interval_maximum():
+    # Example 8's H_p = p^3 - 5p/2 is not monotone: alpha over [u^-, u^+] includes interior extrema
+    rng = np.random.default_rng(8)
+    for _ in range(200):
+        um, up = rng.uniform(-2.5, 2.5, size=2)
+        s = np.linspace(min(um, up), max(um, up), 20001)
+        ref = np.max(np.abs(s**3 - 2.5 * s))
+        got = oracle.node_alpha("nonconvex1d", 1, um, up)[0]
+        assert got == pytest.approx(ref, rel=1e-6, abs=1e-9)
+        assert got >= ref - 1e-12
+    # for monotone-derivative Hamiltonians the node alpha is the end-point maximum
+    for kind, hp in (("burgers1d", lambda p: abs(p + 1)), ("advect1d", lambda p: 1.0)):
+        um, up = -0.7, 1.3
+        assert oracle.node_alpha(kind, 1, um, up)[0] == pytest.approx(max(hp(um), hp(up)))
