@@ -59,7 +59,9 @@ enum {
   ALW_H_ADVECT1D = 3,  /* p               Example 1 */
   ALW_H_BURGERS1D = 4, /* (p+1)^2/2       Example 6 */
   ALW_H_NEGCOS1D = 5,  /* -cos(p+1)       Example 2 */
-  ALW_H_EIKONAL2D = 6  /* sqrt(p^2+q^2+1) Example 12 */
+  ALW_H_EIKONAL2D = 6, /* sqrt(p^2+q^2+1) Example 12 */
+  ALW_H_NONCONVEX1D = 7 /* (p^2-1)(p^2-4)/4 Example 8; non-convex: the node alpha is the
+                           maximum of |H_p| over the interval between the one-sided derivatives */
 };
 
 /* Smoothness indicators of the nonlinear weights (Step 4). */

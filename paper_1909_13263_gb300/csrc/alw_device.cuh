@@ -34,7 +34,7 @@ namespace alw {
 
 enum { BC_PERIODIC = 0, BC_LINEXTRAP = 1 };
 enum { H_BURGERS2D = 0, H_NEGCOS2D = 1, H_SIN2D = 2, H_ADVECT1D = 3, H_BURGERS1D = 4, H_NEGCOS1D = 5,
-       H_EIKONAL2D = 6 };
+       H_EIKONAL2D = 6, H_NONCONVEX1D = 7 };
 enum { W_ARCLEN = 0, W_JP = 1 };
 enum { A_LOCAL_LAGGED = 0, A_LOCAL_EXACT = 1, A_GLOBAL_LAGGED = 2, A_GLOBAL_EXACT = 3, A_FIXED = 4 };
 
@@ -210,11 +210,13 @@ __device__ __forceinline__ T ham_value(int kind, T p, T q) {
     case H_BURGERS1D: { const T z = p + T(1); return T(0.5) * z * z; }
     case H_NEGCOS1D: return -A::cosv(p + T(1));
     case H_EIKONAL2D: return A::sqrtv(p * p + q * q + T(1));
+    case H_NONCONVEX1D: return T(0.25) * (p * p - T(1)) * (p * p - T(4));
     default: return T(0);
   }
 }
 
-// Node alpha: max over the four (u, v) combinations of |H_p| and |H_q|.
+// Node alpha: max over the four (u, v) combinations of |H_p| and |H_q|; for the
+// non-convex Example 8 Hamiltonian, max of |H_p| over the whole interval [u-, u+].
 template <typename T>
 __device__ __forceinline__ void node_alpha(int kind, T um, T up, T vm, T vp, T &ax, T &ay) {
   using A = Arith<T>;
@@ -248,6 +250,14 @@ __device__ __forceinline__ void node_alpha(int kind, T um, T up, T vm, T vp, T &
           my = fmax(my, fabs(vs[b]) * r);
         }
       ax = mx; ay = my;
+    } break;
+    case H_NONCONVEX1D: {
+      // H_p = p^3 - 5p/2; interior extrema of H_p at p = +-sqrt(5/6), where |H_p| = (5/3) sqrt(5/6)
+      const T lo = fmin(um, up), hi = fmax(um, up);
+      const T c = T(0.91287092917527690), hc = c * c * c - T(2.5) * c;
+      T a = fmax(fabs(um * um * um - T(2.5) * um), fabs(up * up * up - T(2.5) * up));
+      if ((lo < c && hi > c) || (lo < -c && hi > -c)) a = fmax(a, fabs(hc));
+      ax = a; ay = T(0);
     } break;
     default: ax = ay = T(0);
   }

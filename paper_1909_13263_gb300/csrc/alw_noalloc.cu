@@ -41,7 +41,8 @@ void *g_scratch_ptr[kMaxDevices] = {};
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-bool is_1d(int k) { return k == ALW_H_ADVECT1D || k == ALW_H_BURGERS1D || k == ALW_H_NEGCOS1D; }
+bool is_1d(int k) { return k == ALW_H_ADVECT1D || k == ALW_H_BURGERS1D || k == ALW_H_NEGCOS1D ||
+                                      k == ALW_H_NONCONVEX1D; }
 
 alw_status err(alw_status st, const char *msg) {
   alw::set_last_error(msg);
@@ -84,7 +85,7 @@ extern "C" alw_status alw_step_noalloc(const alw_grid *grid, const alw_hamiltoni
   if (grid->bc != ALW_BC_PERIODIC && grid->bc != ALW_BC_LINEXTRAP) return err(ALW_EINVAL, "unknown bc");
   if (grid->bc == ALW_BC_LINEXTRAP && (grid->nx < 2 || (grid->dim == 2 && grid->ny < 2)))
     return err(ALW_EINVAL, "linear extrapolation needs at least 2 nodes per direction");
-  if (ham->kind < ALW_H_BURGERS2D || ham->kind > ALW_H_EIKONAL2D || is_1d(ham->kind) != (grid->dim == 1))
+  if (ham->kind < ALW_H_BURGERS2D || ham->kind > ALW_H_NONCONVEX1D || is_1d(ham->kind) != (grid->dim == 1))
     return err(ALW_EINVAL, "Hamiltonian does not match the dimension");
   if (scheme->weights != ALW_W_ARCLEN && scheme->weights != ALW_W_JP) return err(ALW_EINVAL, "unknown weights");
   if (scheme->alpha_mode < ALW_ALPHA_DEFAULT || scheme->alpha_mode > ALW_ALPHA_FIXED)

@@ -154,7 +154,8 @@ struct alw_solver {
 
 namespace {
 
-bool is_1d_ham(int k) { return k == ALW_H_ADVECT1D || k == ALW_H_BURGERS1D || k == ALW_H_NEGCOS1D; }
+bool is_1d_ham(int k) { return k == ALW_H_ADVECT1D || k == ALW_H_BURGERS1D || k == ALW_H_NEGCOS1D ||
+                                      k == ALW_H_NONCONVEX1D; }
 
 int kernel_prec(int precision) {
   return precision == ALW_PREC_FP64 ? P_F64 : precision == ALW_PREC_FP32 ? P_F32 : P_MIXED;
@@ -421,7 +422,7 @@ alw_status alw_create(const alw_grid *grid, const alw_hamiltonian *ham, const al
   if (grid->bc == ALW_BC_LINEXTRAP && (grid->nx < 2 || (grid->dim == 2 && grid->ny < 2)))
     return fail(ALW_EINVAL, "linear extrapolation needs at least 2 nodes per direction");
   if ((long long)grid->nx * grid->ny > (1ll << 31)) return fail(ALW_EINVAL, "grid too large");
-  if (ham->kind < ALW_H_BURGERS2D || ham->kind > ALW_H_EIKONAL2D) return fail(ALW_EINVAL, "unknown Hamiltonian %d", ham->kind);
+  if (ham->kind < ALW_H_BURGERS2D || ham->kind > ALW_H_NONCONVEX1D) return fail(ALW_EINVAL, "unknown Hamiltonian %d", ham->kind);
   if (is_1d_ham(ham->kind) != (grid->dim == 1)) return fail(ALW_EINVAL, "Hamiltonian does not match the dimension");
   if (scheme->weights != ALW_W_ARCLEN && scheme->weights != ALW_W_JP) return fail(ALW_EINVAL, "unknown weights");
   if (!(scheme->eps > 0.0) || !(scheme->cfl > 0.0)) return fail(ALW_EINVAL, "eps and cfl must be > 0");

@@ -44,6 +44,7 @@ CASES_1D = [
     Case(1, 20, 1, "negcos1d", alpha_mode="local_lagged"),
     Case(1, 257, 1, "advect1d", bc="linextrap", alpha_mode="global_lagged"),
     Case(1, 5, 1, "burgers1d", alpha_mode="global_exact"),
+    Case(1, 130, 1, "nonconvex1d", alpha_mode="local_lagged"),
 ]
 
 
