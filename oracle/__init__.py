@@ -26,7 +26,8 @@ _lock = threading.Lock()
 _lib = None
 
 HAM = {"burgers2d": 0, "negcos2d": 1, "sin2d": 2, "advect1d": 3, "burgers1d": 4,
-       "negcos1d": 5, "eikonal2d": 6, "nonconvex1d": 7}
+       "negcos1d": 5, "eikonal2d": 6, "nonconvex1d": 7,
+       "optctrl2d": 8}
 BC = {"periodic": 0, "linextrap": 1}
 WEIGHTS = {"arclength": 0, "jp": 1}
 ALPHA = {"local_lagged": 0, "local_exact": 1, "global_lagged": 2, "global_exact": 3, "fixed": 4}
@@ -38,7 +39,7 @@ class OrcCfg(ctypes.Structure):
                 ("bc", ctypes.c_int32), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
                 ("ham", ctypes.c_int32), ("weights", ctypes.c_int32), ("eps", ctypes.c_double),
                 ("cfl", ctypes.c_double), ("dt_mode", ctypes.c_int32), ("alpha_mode", ctypes.c_int32),
-                ("alpha_fixed", ctypes.c_double * 2)]
+                ("alpha_fixed", ctypes.c_double * 2), ("xlo", ctypes.c_double), ("ylo", ctypes.c_double)]
 
 
 L_FN = ctypes.CFUNCTYPE(None, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
@@ -73,9 +74,9 @@ def lib():
             f.restype = ctypes.c_double
             f.argtypes = [dp, ctypes.c_double, ctypes.c_int, ctypes.c_double, dp, dp, dp]
         L.orc_ham.restype = ctypes.c_int
-        L.orc_ham.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp, dp]
+        L.orc_ham.argtypes = [ctypes.c_int] + [ctypes.c_double] * 4 + [dp, dp, dp]
         L.orc_hhat.restype = ctypes.c_double
-        L.orc_hhat.argtypes = [ctypes.c_int] + [ctypes.c_double] * 6
+        L.orc_hhat.argtypes = [ctypes.c_int] + [ctypes.c_double] * 8
         cp = ctypes.POINTER(OrcCfg)
         L.orc_point_derivs.restype = None
         L.orc_point_derivs.argtypes = [cp, dp, ctypes.c_int, ctypes.c_int, dp]
@@ -95,7 +96,7 @@ def lib():
         L.orc_point_L.restype = ctypes.c_double
         L.orc_point_L.argtypes = [cp, dp, ctypes.c_int, ctypes.c_int, dp]
         L.orc_node_alpha.restype = None
-        L.orc_node_alpha.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 + [dp]
+        L.orc_node_alpha.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 6 + [dp]
         _lib = L
     return _lib
 
@@ -109,7 +110,8 @@ def _f64(a) -> np.ndarray:
 
 
 def make_cfg(*, dim, nx, ny=1, bc="periodic", dx, dy=None, ham, weights="arclength", eps=1e-6,
-             cfl=0.6, dt_mode="cfl", alpha_mode="local_lagged", alpha_fixed=(0.0, 0.0)) -> OrcCfg:
+             cfl=0.6, dt_mode="cfl", alpha_mode="local_lagged", alpha_fixed=(0.0, 0.0),
+             xlo=0.0, ylo=0.0) -> OrcCfg:
     c = OrcCfg()
     c.dim, c.nx, c.ny = dim, nx, (ny if dim == 2 else 1)
     c.bc = BC[bc]
@@ -121,6 +123,7 @@ def make_cfg(*, dim, nx, ny=1, bc="periodic", dx, dy=None, ham, weights="arcleng
     c.dt_mode = DT[dt_mode]
     c.alpha_mode = ALPHA[alpha_mode]
     c.alpha_fixed[0], c.alpha_fixed[1] = alpha_fixed
+    c.xlo, c.ylo = xlo, ylo
     return c
 
 
@@ -146,23 +149,24 @@ def phix_plus(q6, dx, weights="arclength", eps=1e-6):
     return v, cand, beta, omega
 
 
-def ham(kind: str, p: float, q: float = 0.0):
+def ham(kind: str, p: float, q: float = 0.0, x: float = 0.0, y: float = 0.0):
+    """(H, H_p, H_q) at the position (x, y) (only Example 11's H depends on it)."""
     H, Hp, Hq = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
-    st = lib().orc_ham(HAM[kind], p, q, ctypes.byref(H), ctypes.byref(Hp), ctypes.byref(Hq))
+    st = lib().orc_ham(HAM[kind], x, y, p, q, ctypes.byref(H), ctypes.byref(Hp), ctypes.byref(Hq))
     if st:
         raise ValueError(kind)
     return H.value, Hp.value, Hq.value
 
 
-def node_alpha(kind: str, dim: int, um, up, vm=0.0, vp=0.0):
-    """The node-local Lax-Friedrichs alpha pair (alpha_x, alpha_y)."""
+def node_alpha(kind: str, dim: int, um, up, vm=0.0, vp=0.0, x=0.0, y=0.0):
+    """The node-local Lax-Friedrichs alpha pair (alpha_x, alpha_y) at the position (x, y)."""
     out = np.zeros(2)
-    lib().orc_node_alpha(HAM[kind], dim, um, up, vm, vp, _dp(out))
+    lib().orc_node_alpha(HAM[kind], dim, x, y, um, up, vm, vp, _dp(out))
     return out
 
 
-def hhat(kind: str, up, um, vp=0.0, vm=0.0, ax=0.0, ay=0.0) -> float:
-    return lib().orc_hhat(HAM[kind], up, um, vp, vm, ax, ay)
+def hhat(kind: str, up, um, vp=0.0, vm=0.0, ax=0.0, ay=0.0, x=0.0, y=0.0) -> float:
+    return lib().orc_hhat(HAM[kind], x, y, up, um, vp, vm, ax, ay)
 
 
 def derivs(cfg: OrcCfg, phi: np.ndarray):

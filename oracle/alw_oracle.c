@@ -27,7 +27,9 @@
  *       unstated): by default the node's own maximum of |dH/dp| (|dH/dq|)
  *       over the four combinations (u^-/u^+, v^-/v^+) -- the local form
  *       (for the non-convex H of Example 8, whose H_p is not monotone, the
- *       maximum over the whole interval between u^- and u^+),
+ *       maximum over the whole interval between u^- and u^+; for Example
+ *       11, |sin y| and the maximum of |sin x + sign q| over the interval
+ *       between v^- and v^+, both signs when it contains 0),
  *       which reproduces Table 2; the grid-wide maximum of the same values
  *       (global form) and fixed constants are the other modes.  The time
  *       step always uses a grid-wide maximum: of the previous stage
@@ -60,7 +62,8 @@ enum {
   ORC_H_BURGERS1D = 4, /* (p+1)^2/2         Example 6 */
   ORC_H_NEGCOS1D = 5,  /* -cos(p+1)         Example 2 */
   ORC_H_EIKONAL2D = 6, /* sqrt(p^2+q^2+1)   Example 12 */
-  ORC_H_NONCONVEX1D = 7 /* (p^2-1)(p^2-4)/4 Example 8 */
+  ORC_H_NONCONVEX1D = 7, /* (p^2-1)(p^2-4)/4 Example 8 */
+  ORC_H_OPTCTRL2D = 8    /* sin(y)p + (sin(x)+sign q)q - sin^2(y)/2 - (1-cos x)   Example 11 */
 };
 enum {
   ORC_ALPHA_LOCAL_LAGGED = 0,  /* flux: per-node alpha; dt: previous stage's grid max */
@@ -84,6 +87,7 @@ typedef struct {
   int32_t dt_mode;    /* ORC_DT_* */
   int32_t alpha_mode; /* ORC_ALPHA_* */
   double alpha_fixed[2];
+  double xlo, ylo;    /* coordinates of node (0, 0): x_i = xlo + i dx, y_j = ylo + j dy */
 } orc_cfg;
 
 /* ------------------------------------------------------------------------ */
@@ -186,8 +190,11 @@ double orc_phix_plus(const double q[6], double dx, int weights, double eps,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Hamiltonians H(p,q) and partial derivatives (Examples 1-4, 6, 10, 12).   */
-int orc_ham(int kind, double p, double q, double *H, double *Hp, double *Hq) {
+/* Hamiltonians H(x,y,p,q) and partial derivatives in p, q (Examples 1-4, 6, */
+/* 8, 10-12).  Only Example 11 depends on the position (x, y).              */
+static double sign_of(double q) { return q > 0.0 ? 1.0 : (q < 0.0 ? -1.0 : 0.0); }
+
+int orc_ham(int kind, double x, double y, double p, double q, double *H, double *Hp, double *Hq) {
   double h = 0, hp = 0, hq = 0;
   switch (kind) {
     case ORC_H_BURGERS2D: h = 0.5 * (p + q + 1.0) * (p + q + 1.0); hp = hq = p + q + 1.0; break;
@@ -202,6 +209,11 @@ int orc_ham(int kind, double p, double q, double *H, double *Hp, double *Hq) {
     } break;
     case ORC_H_NONCONVEX1D:
       h = 0.25 * (p * p - 1.0) * (p * p - 4.0); hp = p * p * p - 2.5 * p; hq = 0.0; break;
+    case ORC_H_OPTCTRL2D:
+      /* the printed form; (sign q) q = |q| is not differentiable at q = 0, where H_q is
+         returned with sign(0) = 0 (orc_node_alpha handles the generalised derivative) */
+      h = sin(y) * p + (sin(x) + sign_of(q)) * q - 0.5 * sin(y) * sin(y) - (1.0 - cos(x));
+      hp = sin(y); hq = sin(x) + sign_of(q); break;
     default: return ORC_EINVAL;
   }
   if (H) *H = h;
@@ -211,9 +223,9 @@ int orc_ham(int kind, double p, double q, double *H, double *Hp, double *Hq) {
 }
 
 /* Lax-Friedrichs numerical Hamiltonian, applied per direction in 2D. */
-double orc_hhat(int kind, double up, double um, double vp, double vm, double ax, double ay) {
+double orc_hhat(int kind, double x, double y, double up, double um, double vp, double vm, double ax, double ay) {
   double H = 0.0;
-  orc_ham(kind, 0.5 * (up + um), 0.5 * (vp + vm), &H, NULL, NULL);
+  orc_ham(kind, x, y, 0.5 * (up + um), 0.5 * (vp + vm), &H, NULL, NULL);
   return H - ax * 0.5 * (up - um) - ay * 0.5 * (vp - vm);
 }
 
@@ -265,11 +277,31 @@ void orc_derivs(const orc_cfg *cfg, const double *phi, double *um, double *up, d
     }
 }
 
+/* Coordinates of the node with row-major index k (reading R7). */
+static double node_x(const orc_cfg *cfg, ptrdiff_t k) { return cfg->xlo + (double)(k % cfg->nx) * cfg->dx; }
+static double node_y(const orc_cfg *cfg, ptrdiff_t k) {
+  return cfg->dim == 2 ? cfg->ylo + (double)(k / cfg->nx) * cfg->dy : 0.0;
+}
+
 /* Reading R5, local form: the node's own alpha = max over the four (u, v)
  * combinations at that node of |H_p| (resp. |H_q|). */
-void orc_node_alpha(int ham, int dim, double um, double up, double vm, double vp, double out[2]) {
+void orc_node_alpha(int ham, int dim, double x, double y, double um, double up, double vm, double vp,
+                    double out[2]) {
   const double us[2] = {um, up}, vs[2] = {vm, vp};
   double ax = 0.0, ay = 0.0;
+  if (ham == ORC_H_OPTCTRL2D) {
+    /* H_p = sin y does not depend on (p, q).  H_q = sin x + sign q is piecewise constant: over
+       [min(v), max(v)] its values are sin x + s for s in the signs the interval holds, where an
+       interval containing q = 0 holds both (the generalised derivative of |q| at 0 is [-1, 1]) */
+    const double lo = fmin(vm, vp), hi = fmax(vm, vp);
+    ax = fabs(sin(y));
+    if (lo <= 0.0 && hi >= 0.0) ay = fmax(fabs(sin(x) + 1.0), fabs(sin(x) - 1.0));
+    else ay = fabs(sin(x) + sign_of(lo));
+    if (isnan(um) || isnan(up) || isnan(vm) || isnan(vp)) ax = ay = NAN;
+    out[0] = ax;
+    out[1] = ay;
+    return;
+  }
   if (ham == ORC_H_NONCONVEX1D) {
     /* H_p = p^3 - 5p/2 is not monotone: its largest modulus on [min(u), max(u)] is at an end or
        where H_pp = 3p^2 - 5/2 vanishes, p = +-sqrt(5/6) */
@@ -278,7 +310,7 @@ void orc_node_alpha(int ham, int dim, double um, double up, double vm, double vp
     for (int k = 0; k < 4; ++k) {
       if (k >= 2 && !(cand[k] > lo && cand[k] < hi)) continue;
       double hp;
-      orc_ham(ham, cand[k], 0.0, NULL, &hp, NULL);
+      orc_ham(ham, x, y, cand[k], 0.0, NULL, &hp, NULL);
       if (fabs(hp) > ax || isnan(hp)) ax = fabs(hp);
     }
     if (isnan(um) || isnan(up)) ax = NAN;
@@ -289,7 +321,7 @@ void orc_node_alpha(int ham, int dim, double um, double up, double vm, double vp
   for (int a = 0; a < 2; ++a)
     for (int b = 0; b < 2; ++b) {
       double hp, hq;
-      orc_ham(ham, us[a], vs[b], NULL, &hp, &hq);
+      orc_ham(ham, x, y, us[a], vs[b], NULL, &hp, &hq);
       if (fabs(hp) > ax || isnan(hp)) ax = fabs(hp);
       if (fabs(hq) > ay || isnan(hq)) ay = fabs(hq);
     }
@@ -306,7 +338,7 @@ int orc_alpha_max(const orc_cfg *cfg, const double *um, const double *up, const 
   const ptrdiff_t n = (ptrdiff_t)cfg->nx * cfg->ny;
   for (ptrdiff_t k = 0; k < n; ++k) {
     double a[2];
-    orc_node_alpha(cfg->ham, cfg->dim, um[k], up[k], vm[k], vp[k], a);
+    orc_node_alpha(cfg->ham, cfg->dim, node_x(cfg, k), node_y(cfg, k), um[k], up[k], vm[k], vp[k], a);
     if (!isfinite(a[0]) || !isfinite(a[1])) bad = 1;
     if (a[0] > ax) ax = a[0];
     if (a[1] > ay) ay = a[1];
@@ -324,8 +356,9 @@ void orc_L_from_derivs(const orc_cfg *cfg, const double *um, const double *up, c
   const int local = (cfg->alpha_mode == ORC_ALPHA_LOCAL_LAGGED || cfg->alpha_mode == ORC_ALPHA_LOCAL_EXACT);
   for (ptrdiff_t k = 0; k < n; ++k) {
     double a[2] = {alpha[0], alpha[1]};
-    if (local) orc_node_alpha(cfg->ham, cfg->dim, um[k], up[k], vm[k], vp[k], a);
-    L[k] = -orc_hhat(cfg->ham, up[k], um[k], vp[k], vm[k], a[0], cfg->dim == 2 ? a[1] : 0.0);
+    const double x = node_x(cfg, k), y = node_y(cfg, k);
+    if (local) orc_node_alpha(cfg->ham, cfg->dim, x, y, um[k], up[k], vm[k], vp[k], a);
+    L[k] = -orc_hhat(cfg->ham, x, y, up[k], um[k], vp[k], vm[k], a[0], cfg->dim == 2 ? a[1] : 0.0);
   }
 }
 
@@ -468,6 +501,7 @@ double orc_point_L(const orc_cfg *cfg, const double *phi, int i, int j, const do
   double d[4], a[2] = {alpha[0], alpha[1]};
   orc_point_derivs(cfg, phi, i, j, d);
   if (cfg->alpha_mode == ORC_ALPHA_LOCAL_LAGGED || cfg->alpha_mode == ORC_ALPHA_LOCAL_EXACT)
-    orc_node_alpha(cfg->ham, cfg->dim, d[0], d[1], d[2], d[3], a);
-  return -orc_hhat(cfg->ham, d[1], d[0], d[3], d[2], a[0], cfg->dim == 2 ? a[1] : 0.0);
+    orc_node_alpha(cfg->ham, cfg->dim, cfg->xlo + i * cfg->dx, cfg->ylo + j * cfg->dy, d[0], d[1], d[2], d[3], a);
+  return -orc_hhat(cfg->ham, cfg->xlo + i * cfg->dx, cfg->ylo + j * cfg->dy, d[1], d[0], d[3], d[2], a[0],
+                   cfg->dim == 2 ? a[1] : 0.0);
 }

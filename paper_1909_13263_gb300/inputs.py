@@ -118,6 +118,7 @@ PROBLEMS = {
     "ex12_eikonal2d": Problem("ex12_eikonal2d", 2, "eikonal2d", 0.0, 1.0, "periodic", 0.6, "eikonal"),
     "ex5_corners": Problem("ex5_corners", 1, "advect1d", -1.0, 1.0, "periodic", 2.0, "corners"),
     "ex8_nonconvex1d": Problem("ex8_nonconvex1d", 1, "nonconvex1d", -1.0, 1.0, "periodic", 1.0, "abs"),
+    "ex11_optctrl2d": Problem("ex11_optctrl2d", 2, "optctrl2d", -math.pi, math.pi, "periodic", 1.0, "zero"),
 }
 
 
@@ -133,6 +134,8 @@ def initial(problem: Problem, n: int, theta: float = 0.0):
         return phi0_riemann_2d(x, x), dx
     if problem.phi0 == "eikonal":
         return phi0_eikonal_2d(x, x), dx
+    if problem.phi0 == "zero":
+        return np.zeros((n, n)), dx
     raise ValueError(problem.phi0)
 
 

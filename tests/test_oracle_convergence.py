@@ -174,3 +174,31 @@ def test_example8_nonconvex_matches_hopf_formula(weights):
         if n == 400:
             assert e.max() < 5e-3
     assert l1[0] / l1[1] > 1.7 and l1[1] / l1[2] > 1.7, l1
+
+
+def _taylor_example11(X, Y, t):
+    # phi0 = 0 and phi_t = -H(x, y, grad phi): phi = t l - t^2/2 (sin y l_x + sin x l_y + |l_y|) + O(t^3)
+    # with l = sin^2(y)/2 + 1 - cos x the running cost (H(x, y, 0) = -l)
+    lx, ly = np.sin(X), np.sin(Y) * np.cos(Y)
+    ell = 0.5 * np.sin(Y) ** 2 + 1.0 - np.cos(X)
+    return t * ell - 0.5 * t * t * (np.sin(Y) * lx + np.sin(X) * ly + np.abs(ly))
+
+
+@pytest.mark.parametrize("weights", ["arclength", "jp"])
+def test_example11_short_time_expansion(weights):
+    # Example 11 on [-pi, pi)^2 from phi0 = 0: the oracle matches the two-term expansion in t
+    # with an O(t^3) remainder (ratio ~ 8 per halving of t), which fails if any term of H,
+    # its position dependence or the sign convention of (sign q) q is wrong
+    n = 40
+    x, dx = inputs.axis(n, -np.pi, np.pi, "periodic")
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    errs = []
+    for tau in (0.1, 0.05):
+        cfg = oracle.make_cfg(dim=2, nx=n, ny=n, dx=dx, dy=dx, ham="optctrl2d", weights=weights,
+                              alpha_mode="global_lagged", xlo=-np.pi, ylo=-np.pi)
+        phi, _, t, _, st = oracle.solve(cfg, np.zeros((n, n)), tau)
+        assert st == 0 and t == tau
+        e = np.abs(phi - _taylor_example11(X, Y, tau)).max()
+        assert e < 1.5 * tau**3, (tau, e)
+        errs.append(e)
+    assert errs[0] / errs[1] > 6.0, errs

@@ -220,14 +220,17 @@ def test_weights_convex_on_rough_data():
 
 
 HAMS2 = {
-    "burgers2d": (lambda p, q: 0.5 * (p + q + 1) ** 2),
-    "negcos2d": (lambda p, q: -np.cos(p + q + 1)),
-    "sin2d": (lambda p, q: np.sin(p + q)),
-    "eikonal2d": (lambda p, q: np.sqrt(p * p + q * q + 1)),
-    "advect1d": (lambda p, q: p),
-    "burgers1d": (lambda p, q: 0.5 * (p + 1) ** 2),
-    "negcos1d": (lambda p, q: -np.cos(p + 1)),
-    "nonconvex1d": (lambda p, q: 0.25 * (p * p - 1) * (p * p - 4)),
+    "burgers2d": (lambda p, q, x, y: 0.5 * (p + q + 1) ** 2),
+    "negcos2d": (lambda p, q, x, y: -np.cos(p + q + 1)),
+    "sin2d": (lambda p, q, x, y: np.sin(p + q)),
+    "eikonal2d": (lambda p, q, x, y: np.sqrt(p * p + q * q + 1)),
+    "advect1d": (lambda p, q, x, y: p),
+    "burgers1d": (lambda p, q, x, y: 0.5 * (p + 1) ** 2),
+    "negcos1d": (lambda p, q, x, y: -np.cos(p + 1)),
+    "nonconvex1d": (lambda p, q, x, y: 0.25 * (p * p - 1) * (p * p - 4)),
+    # Example 11 with (sign q) q written as |q|
+    "optctrl2d": (lambda p, q, x, y: np.sin(y) * p + np.sin(x) * q + abs(q) - 0.5 * np.sin(y) ** 2
+                  - (1 - np.cos(x))),
 }
 
 
@@ -237,11 +240,12 @@ def test_hamiltonian_values_and_partials(kind):
     f = HAMS2[kind]
     for _ in range(20):
         p, q = rng.normal(size=2) * 2
-        H, Hp, Hq = oracle.ham(kind, p, q)
-        assert H == pytest.approx(f(p, q), rel=1e-14, abs=1e-14)
+        x, y = rng.uniform(-np.pi, np.pi, size=2)
+        H, Hp, Hq = oracle.ham(kind, p, q, x, y)
+        assert H == pytest.approx(f(p, q, x, y), rel=1e-14, abs=1e-14)
         h = 1e-6
-        assert Hp == pytest.approx((f(p + h, q) - f(p - h, q)) / (2 * h), rel=1e-6, abs=1e-7)
-        assert Hq == pytest.approx((f(p, q + h) - f(p, q - h)) / (2 * h), rel=1e-6, abs=1e-7)
+        assert Hp == pytest.approx((f(p + h, q, x, y) - f(p - h, q, x, y)) / (2 * h), rel=1e-6, abs=1e-7)
+        assert Hq == pytest.approx((f(p, q + h, x, y) - f(p, q - h, x, y)) / (2 * h), rel=1e-6, abs=1e-7)
 
 
 @pytest.mark.parametrize("kind", list(HAMS2))
@@ -249,15 +253,42 @@ def test_lf_flux_consistent_and_monotone(kind):
     rng = np.random.default_rng(4)
     for _ in range(20):
         u, v = rng.normal(size=2)
-        H = oracle.ham(kind, u, v)[0]
-        assert oracle.hhat(kind, u, u, v, v, 3.0, 3.0) == pytest.approx(H, rel=1e-15, abs=1e-15)
+        x, y = rng.uniform(-np.pi, np.pi, size=2)
+        H = oracle.ham(kind, u, v, x, y)[0]
+        assert oracle.hhat(kind, u, u, v, v, 3.0, 3.0, x, y) == pytest.approx(H, rel=1e-15, abs=1e-15)
         # non-increasing in u^+, non-decreasing in u^- when alpha bounds |H_p| on the range
         up, um, vp, vm = rng.normal(size=4) * 0.5
         a = 4.0  # bounds |H_p|, |H_q| of every kind on |p|, |q| <= 1.5
         h = 1e-6
-        d_up = oracle.hhat(kind, up + h, um, vp, vm, a, a) - oracle.hhat(kind, up, um, vp, vm, a, a)
-        d_um = oracle.hhat(kind, up, um + h, vp, vm, a, a) - oracle.hhat(kind, up, um, vp, vm, a, a)
-        assert d_up <= 1e-15 and d_um >= -1e-15
+        hh = lambda *d: oracle.hhat(kind, *d, a, a, x, y)
+        d_up = hh(up + h, um, vp, vm) - hh(up, um, vp, vm)
+        d_um = hh(up, um + h, vp, vm) - hh(up, um, vp, vm)
+        d_vp = hh(up, um, vp + h, vm) - hh(up, um, vp, vm)
+        d_vm = hh(up, um, vp, vm + h) - hh(up, um, vp, vm)
+        assert d_up <= 1e-15 and d_um >= -1e-15 and d_vp <= 1e-15 and d_vm >= -1e-15
+
+
+def test_optimal_control_alpha_bounds_the_slopes_of_H():
+    # Example 11: alpha_x = |sin y|; alpha_y = the largest |dH/dq| over the interval between
+    # v^- and v^+, where the kink of |q| at 0 contributes both one-sided slopes sin x +- 1
+    f = HAMS2["optctrl2d"]
+    rng = np.random.default_rng(11)
+    for _ in range(300):
+        x, y = rng.uniform(-np.pi, np.pi, size=2)
+        um, up = rng.normal(size=2)
+        vm, vp = rng.normal(size=2) * rng.choice([1e-3, 0.3, 2.0])
+        if rng.random() < 0.1:
+            vm = vp = 0.0
+        ax, ay = oracle.node_alpha("optctrl2d", 2, um, up, vm, vp, x, y)
+        assert ax == pytest.approx(abs(np.sin(y)), abs=1e-15)
+        lo, hi = min(vm, vp), max(vm, vp)
+        # one-sided difference quotients of H in q, sampled across [lo, hi]
+        qs = np.linspace(lo, hi, 101)
+        h = 1e-7
+        slopes = [abs(f(0.1, qq + s * h, x, y) - f(0.1, qq, x, y)) / h for qq in qs for s in (1, -1)]
+        assert ay == pytest.approx(max(slopes), rel=1e-5, abs=1e-6)
+        # the flux built on it is monotone over the whole interval
+        assert ay >= max(slopes) - 1e-6
 
 
 def test_rk3_amplification_polynomial():
