@@ -60,8 +60,13 @@ enum {
   ALW_H_BURGERS1D = 4, /* (p+1)^2/2       Example 6 */
   ALW_H_NEGCOS1D = 5,  /* -cos(p+1)       Example 2 */
   ALW_H_EIKONAL2D = 6, /* sqrt(p^2+q^2+1) Example 12 */
-  ALW_H_NONCONVEX1D = 7 /* (p^2-1)(p^2-4)/4 Example 8; non-convex: the node alpha is the
-                           maximum of |H_p| over the interval between the one-sided derivatives */
+  ALW_H_NONCONVEX1D = 7, /* (p^2-1)(p^2-4)/4 Example 8; non-convex: the node alpha is the
+                            maximum of |H_p| over the interval between the one-sided derivatives */
+  ALW_H_OPTCTRL2D = 8    /* sin(y)p + (sin(x)+sign q)q - sin^2(y)/2 - (1-cos x)   Example 11;
+                            depends on the node position x_i = xlo + i dx, y_j = ylo + j dy;
+                            alpha_x = |sin y|, alpha_y = max |sin x + s| over the signs s of the
+                            interval between v^- and v^+ (both when it contains 0).  Single
+                            solvers only (batches and the server reject it). */
 };
 
 /* Smoothness indicators of the nonlinear weights (Step 4). */

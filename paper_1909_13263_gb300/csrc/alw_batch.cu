@@ -268,6 +268,8 @@ alw_status build(alw_batch *b) {
     d.dy = (float)dy;
     d.rdx = (float)(1.0 / dx);
     d.rdy = (float)(1.0 / dy);
+    d.xlo = (float)pd.grid.xlo;
+    d.ylo = (float)pd.grid.ylo;
     d.lx = b->scheme.dt_mode == ALW_DT_DX53 ? std::pow(dx, 5.0 / 3.0) : dx;
     d.ly = b->scheme.dt_mode == ALW_DT_DX53 ? std::pow(dy, 5.0 / 3.0) : dy;
     pitch = std::max(pitch, d.tiles_x * kTile2DX + 2 * GX);

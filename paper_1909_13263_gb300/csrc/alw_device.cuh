@@ -34,7 +34,7 @@ namespace alw {
 
 enum { BC_PERIODIC = 0, BC_LINEXTRAP = 1 };
 enum { H_BURGERS2D = 0, H_NEGCOS2D = 1, H_SIN2D = 2, H_ADVECT1D = 3, H_BURGERS1D = 4, H_NEGCOS1D = 5,
-       H_EIKONAL2D = 6, H_NONCONVEX1D = 7 };
+       H_EIKONAL2D = 6, H_NONCONVEX1D = 7, H_OPTCTRL2D = 8 };
 enum { W_ARCLEN = 0, W_JP = 1 };
 enum { A_LOCAL_LAGGED = 0, A_LOCAL_EXACT = 1, A_GLOBAL_LAGGED = 2, A_GLOBAL_EXACT = 3, A_FIXED = 4 };
 
@@ -199,8 +199,9 @@ __device__ __forceinline__ void weno_sweep(const T (&v)[K + 5], T rdx, T dx, T e
 // --------------------------------------------------------------------------
 // Hamiltonians (runtime kind, uniform across the grid).
 
+// (x, y) is the node's position; only Example 11's H depends on it.
 template <typename T>
-__device__ __forceinline__ T ham_value(int kind, T p, T q) {
+__device__ __forceinline__ T ham_value(int kind, T p, T q, T x, T y) {
   using A = Arith<T>;
   switch (kind) {
     case H_BURGERS2D: { const T z = p + q + T(1); return T(0.5) * z * z; }
@@ -211,6 +212,11 @@ __device__ __forceinline__ T ham_value(int kind, T p, T q) {
     case H_NEGCOS1D: return -A::cosv(p + T(1));
     case H_EIKONAL2D: return A::sqrtv(p * p + q * q + T(1));
     case H_NONCONVEX1D: return T(0.25) * (p * p - T(1)) * (p * p - T(4));
+    case H_OPTCTRL2D: {
+      // sin(y) p + (sin(x) + sign q) q - sin^2(y)/2 - (1 - cos x), with (sign q) q = |q|
+      const T sy = A::sinv(y);
+      return sy * p + A::sinv(x) * q + fabs(q) - T(0.5) * sy * sy - (T(1) - A::cosv(x));
+    }
     default: return T(0);
   }
 }
@@ -218,7 +224,7 @@ __device__ __forceinline__ T ham_value(int kind, T p, T q) {
 // Node alpha: max over the four (u, v) combinations of |H_p| and |H_q|; for the
 // non-convex Example 8 Hamiltonian, max of |H_p| over the whole interval [u-, u+].
 template <typename T>
-__device__ __forceinline__ void node_alpha(int kind, T um, T up, T vm, T vp, T &ax, T &ay) {
+__device__ __forceinline__ void node_alpha(int kind, T um, T up, T vm, T vp, T x, T y, T &ax, T &ay) {
   using A = Arith<T>;
   switch (kind) {
     case H_BURGERS2D: {
@@ -258,6 +264,13 @@ __device__ __forceinline__ void node_alpha(int kind, T um, T up, T vm, T vp, T &
       T a = fmax(fabs(um * um * um - T(2.5) * um), fabs(up * up * up - T(2.5) * up));
       if ((lo < c && hi > c) || (lo < -c && hi > -c)) a = fmax(a, fabs(hc));
       ax = a; ay = T(0);
+    } break;
+    case H_OPTCTRL2D: {
+      // H_p = sin y; H_q = sin x + sign q over [min v, max v], both signs when the interval
+      // contains the kink of |q| at 0
+      const T sx = A::sinv(x), lo = fmin(vm, vp), hi = fmax(vm, vp);
+      ax = fabs(A::sinv(y));
+      ay = (lo <= T(0) && hi >= T(0)) ? fabs(sx) + T(1) : fabs(sx + (lo > T(0) ? T(1) : T(-1)));
     } break;
     default: ax = ay = T(0);
   }

@@ -43,6 +43,7 @@ struct StageParams {
   int zero_slot;         // slot the epilogue clears for a later stage, -1 none
   int dt_slot;           // slot the stage-1 dt rule reads (lagged: 2, exact: 3)
   double dx, dy, rdx, rdy, eps;
+  double xlo, ylo;       // coordinates of node (0, 0) (position-dependent Hamiltonians)
   double cfl, lx, ly;    // dt = cfl / (ax/lx + ay/ly)
   double alpha_fixed[2];
   double dt_value;       // LOOP_STAGE: the dt of this stage

@@ -43,6 +43,7 @@ static int launch2d_h(const Stage2DParams &prm, cudaStream_t s) {
     case H_NEGCOS2D: return launch2d_one<PREC, W, H_NEGCOS2D>(prm, s);
     case H_SIN2D: return launch2d_one<PREC, W, H_SIN2D>(prm, s);
     case H_EIKONAL2D: return launch2d_one<PREC, W, H_EIKONAL2D>(prm, s);
+    case H_OPTCTRL2D: return launch2d_one<PREC, W, H_OPTCTRL2D>(prm, s);
     default: return (int)cudaErrorInvalidValue;
   }
 }

@@ -85,7 +85,7 @@ extern "C" alw_status alw_step_noalloc(const alw_grid *grid, const alw_hamiltoni
   if (grid->bc != ALW_BC_PERIODIC && grid->bc != ALW_BC_LINEXTRAP) return err(ALW_EINVAL, "unknown bc");
   if (grid->bc == ALW_BC_LINEXTRAP && (grid->nx < 2 || (grid->dim == 2 && grid->ny < 2)))
     return err(ALW_EINVAL, "linear extrapolation needs at least 2 nodes per direction");
-  if (ham->kind < ALW_H_BURGERS2D || ham->kind > ALW_H_NONCONVEX1D || is_1d(ham->kind) != (grid->dim == 1))
+  if (ham->kind < ALW_H_BURGERS2D || ham->kind > ALW_H_OPTCTRL2D || is_1d(ham->kind) != (grid->dim == 1))
     return err(ALW_EINVAL, "Hamiltonian does not match the dimension");
   if (scheme->weights != ALW_W_ARCLEN && scheme->weights != ALW_W_JP) return err(ALW_EINVAL, "unknown weights");
   if (scheme->alpha_mode < ALW_ALPHA_DEFAULT || scheme->alpha_mode > ALW_ALPHA_FIXED)
@@ -142,6 +142,7 @@ extern "C" alw_status alw_step_noalloc(const alw_grid *grid, const alw_hamiltoni
     p.alpha_mode = amode; p.loop_mode = LOOP_STAGE; p.stage = stage;
     p.src_of = stage == 0 ? src_of : stage;
     p.dx = dx; p.dy = dy; p.rdx = 1.0 / dx; p.rdy = 1.0 / dy; p.eps = scheme->eps;
+    p.xlo = grid->xlo; p.ylo = grid->dim == 2 ? grid->ylo : 0.0;
     p.cfl = scheme->cfl; p.lx = dx; p.ly = dy;
     p.alpha_fixed[0] = scheme->alpha_fixed[0]; p.alpha_fixed[1] = scheme->alpha_fixed[1];
     p.dt_value = dt; p.state = ds; p.dt_slot = 2;

@@ -16,6 +16,7 @@ struct InstDesc {
   int ham, bc;           // Hamiltonian kind, boundary condition
   int ntiles;            // tiles_x * tiles_y
   float dx, dy, rdx, rdy;
+  float xlo, ylo;        // coordinates of node (0, 0) (position-dependent Hamiltonians)
   double lx, ly;         // dt = cfl / (ax/lx + ay/ly)
   DevState *st;          // this instance's device-side time and alpha state
 };

@@ -184,6 +184,8 @@ int launch_stage(const alw_solver *s, const StageParams &p) {
     d.dy = (float)s->dy;
     d.rdx = (float)(1.0 / s->dx);
     d.rdy = (float)(1.0 / s->dy);
+    d.xlo = (float)s->grid.xlo;
+    d.ylo = (float)s->grid.ylo;
     d.lx = s->lx;
     d.ly = s->ly;
     d.st = s->st;
@@ -229,6 +231,8 @@ StageParams make_params(const alw_solver *s, int stage, int src_of, int loop_mod
   p.rdx = 1.0 / s->dx;
   p.rdy = 1.0 / s->dy;
   p.eps = s->scheme.eps;
+  p.xlo = s->grid.xlo;
+  p.ylo = s->dim == 2 ? s->grid.ylo : 0.0;
   p.cfl = s->scheme.cfl;
   p.lx = s->lx;
   p.ly = s->ly;
@@ -422,7 +426,7 @@ alw_status alw_create(const alw_grid *grid, const alw_hamiltonian *ham, const al
   if (grid->bc == ALW_BC_LINEXTRAP && (grid->nx < 2 || (grid->dim == 2 && grid->ny < 2)))
     return fail(ALW_EINVAL, "linear extrapolation needs at least 2 nodes per direction");
   if ((long long)grid->nx * grid->ny > (1ll << 31)) return fail(ALW_EINVAL, "grid too large");
-  if (ham->kind < ALW_H_BURGERS2D || ham->kind > ALW_H_NONCONVEX1D) return fail(ALW_EINVAL, "unknown Hamiltonian %d", ham->kind);
+  if (ham->kind < ALW_H_BURGERS2D || ham->kind > ALW_H_OPTCTRL2D) return fail(ALW_EINVAL, "unknown Hamiltonian %d", ham->kind);
   if (is_1d_ham(ham->kind) != (grid->dim == 1)) return fail(ALW_EINVAL, "Hamiltonian does not match the dimension");
   if (scheme->weights != ALW_W_ARCLEN && scheme->weights != ALW_W_JP) return fail(ALW_EINVAL, "unknown weights");
   if (!(scheme->eps > 0.0) || !(scheme->cfl > 0.0)) return fail(ALW_EINVAL, "eps and cfl must be > 0");

@@ -224,6 +224,8 @@ int admit_one(alw_server *s, Request *r, int slot) {
   d.dy = (float)dy;
   d.rdx = (float)(1.0 / dx);
   d.rdy = (float)(1.0 / dy);
+  d.xlo = (float)r->grid.xlo;
+  d.ylo = (float)r->grid.ylo;
   d.lx = s->scheme.dt_mode == ALW_DT_DX53 ? std::pow(dx, 5.0 / 3.0) : dx;
   d.ly = s->scheme.dt_mode == ALW_DT_DX53 ? std::pow(dy, 5.0 / 3.0) : dy;
   d.st = s->d_state + slot;

@@ -114,13 +114,14 @@ __global__ void __launch_bounds__(Shape<PREC, DIM>::NT) stage_kernel(const Stage
     const int gi = tx0 + lxn, gj = ty0 + lyn;
     if (gi >= p.nx || gj >= p.ny) return;
     C ax, ay;
-    node_alpha<C>(p.ham, um, up, vm, vp, ax, ay);
+    const C xn = C(p.xlo + gi * p.dx), yn = C(p.ylo + gj * p.dy);
+    node_alpha<C>(p.ham, um, up, vm, vp, xn, yn, ax, ay);
     if (!(isfinite(ax) && isfinite(ay))) bad = true;
     amx = fmax(amx, ax);
     amy = fmax(amy, ay);
     if (p.stage == 0) return;
     const C aX = local_alpha ? ax : fax, aY = local_alpha ? ay : fay;
-    const C H = ham_value<C>(p.ham, C(0.5) * (up + um), C(0.5) * (vp + vm));
+    const C H = ham_value<C>(p.ham, C(0.5) * (up + um), C(0.5) * (vp + vm), xn, yn);
     const C L = -((H - aX * C(0.5) * (up - um)) - aY * C(0.5) * (vp - vm));
     const int sidx = ((DIM == 2) ? lyn + 3 : 0) * SW + lxn + 4;
     if (PREC == P_MIXED) {

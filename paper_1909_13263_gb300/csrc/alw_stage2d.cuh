@@ -32,35 +32,39 @@ namespace alw {
 // Hamiltonians of the 2D examples in float (compile-time kind).
 template <int H> struct Ham2;
 template <> struct Ham2<H_BURGERS2D> {
-  __device__ __forceinline__ static float value(float p, float q) {
+  __device__ __forceinline__ static float value(float p, float q, float, float) {
     const float z = p + q + 1.0f;
     return 0.5f * z * z;
   }
-  __device__ __forceinline__ static void alpha(float um, float up, float vm, float vp, float &ax, float &ay) {
+  __device__ __forceinline__ static void alpha(float um, float up, float vm, float vp, float, float, float &ax,
+                                                    float &ay) {
     const float a = fabsf(um + vm + 1.0f), b = fabsf(um + vp + 1.0f);
     const float c = fabsf(up + vm + 1.0f), d = fabsf(up + vp + 1.0f);
     ax = ay = fmaxf(fmaxf(a, b), fmaxf(c, d));
   }
 };
 template <> struct Ham2<H_NEGCOS2D> {
-  __device__ __forceinline__ static float value(float p, float q) { return -__cosf(p + q + 1.0f); }
-  __device__ __forceinline__ static void alpha(float um, float up, float vm, float vp, float &ax, float &ay) {
+  __device__ __forceinline__ static float value(float p, float q, float, float) { return -__cosf(p + q + 1.0f); }
+  __device__ __forceinline__ static void alpha(float um, float up, float vm, float vp, float, float, float &ax,
+                                                    float &ay) {
     const float a = fabsf(__sinf(um + vm + 1.0f)), b = fabsf(__sinf(um + vp + 1.0f));
     const float c = fabsf(__sinf(up + vm + 1.0f)), d = fabsf(__sinf(up + vp + 1.0f));
     ax = ay = fmaxf(fmaxf(a, b), fmaxf(c, d));
   }
 };
 template <> struct Ham2<H_SIN2D> {
-  __device__ __forceinline__ static float value(float p, float q) { return __sinf(p + q); }
-  __device__ __forceinline__ static void alpha(float um, float up, float vm, float vp, float &ax, float &ay) {
+  __device__ __forceinline__ static float value(float p, float q, float, float) { return __sinf(p + q); }
+  __device__ __forceinline__ static void alpha(float um, float up, float vm, float vp, float, float, float &ax,
+                                                    float &ay) {
     const float a = fabsf(__cosf(um + vm)), b = fabsf(__cosf(um + vp));
     const float c = fabsf(__cosf(up + vm)), d = fabsf(__cosf(up + vp));
     ax = ay = fmaxf(fmaxf(a, b), fmaxf(c, d));
   }
 };
 template <> struct Ham2<H_EIKONAL2D> {
-  __device__ __forceinline__ static float value(float p, float q) { return sqrtf(fmaf(p, p, fmaf(q, q, 1.0f))); }
-  __device__ __forceinline__ static void alpha(float um, float up, float vm, float vp, float &ax, float &ay) {
+  __device__ __forceinline__ static float value(float p, float q, float, float) { return sqrtf(fmaf(p, p, fmaf(q, q, 1.0f))); }
+  __device__ __forceinline__ static void alpha(float um, float up, float vm, float vp, float, float, float &ax,
+                                                    float &ay) {
     const float r00 = rsqrtf(fmaf(um, um, fmaf(vm, vm, 1.0f))), r01 = rsqrtf(fmaf(um, um, fmaf(vp, vp, 1.0f)));
     const float r10 = rsqrtf(fmaf(up, up, fmaf(vm, vm, 1.0f))), r11 = rsqrtf(fmaf(up, up, fmaf(vp, vp, 1.0f)));
     ax = fmaxf(fmaxf(fabsf(um) * r00, fabsf(um) * r01), fmaxf(fabsf(up) * r10, fabsf(up) * r11));
@@ -68,30 +72,53 @@ template <> struct Ham2<H_EIKONAL2D> {
   }
 };
 
+// Example 11 (optimal control): the only Hamiltonian that depends on the node position (x, y).
+template <> struct Ham2<H_OPTCTRL2D> {
+  __device__ __forceinline__ static float value(float p, float q, float x, float y) {
+    float sx, cx, sy, cy;
+    __sincosf(x, &sx, &cx);
+    __sincosf(y, &sy, &cy);
+    // sin(y) p + (sin(x) + sign q) q - sin^2(y)/2 - (1 - cos x), with (sign q) q = |q|
+    return fmaf(sy, p, fmaf(sx, q, fabsf(q))) - fmaf(0.5f * sy, sy, 1.0f - cx);
+  }
+  __device__ __forceinline__ static void alpha(float, float, float vm, float vp, float x, float y, float &ax,
+                                               float &ay) {
+    // H_p = sin y; H_q = sin x + sign q over [min v, max v], both signs when it contains q = 0
+    const float sx = __sinf(x), lo = fminf(vm, vp), hi = fmaxf(vm, vp);
+    ax = fabsf(__sinf(y));
+    ay = (lo <= 0.0f && hi >= 0.0f) ? fabsf(sx) + 1.0f : fabsf(sx + (lo > 0.0f ? 1.0f : -1.0f));
+  }
+};
+
 // Compile-time kind H >= 0, or H = -1: the kind is read per instance (batches mixing Hamiltonians).
 template <int H> struct HamSel {
   int kind;
-  __device__ __forceinline__ float value(float p, float q) const { return Ham2<H>::value(p, q); }
-  __device__ __forceinline__ void alpha(float um, float up, float vm, float vp, float &ax, float &ay) const {
-    Ham2<H>::alpha(um, up, vm, vp, ax, ay);
+  __device__ __forceinline__ float value(float p, float q, float x, float y) const {
+    return Ham2<H>::value(p, q, x, y);
+  }
+  __device__ __forceinline__ void alpha(float um, float up, float vm, float vp, float x, float y, float &ax,
+                                        float &ay) const {
+    Ham2<H>::alpha(um, up, vm, vp, x, y, ax, ay);
   }
 };
+// batches and the server hold position-free Hamiltonians only (checked on the host)
 template <> struct HamSel<-1> {
   int kind;
-  __device__ __forceinline__ float value(float p, float q) const {
+  __device__ __forceinline__ float value(float p, float q, float x, float y) const {
     switch (kind) {
-      case H_NEGCOS2D: return Ham2<H_NEGCOS2D>::value(p, q);
-      case H_SIN2D: return Ham2<H_SIN2D>::value(p, q);
-      case H_EIKONAL2D: return Ham2<H_EIKONAL2D>::value(p, q);
-      default: return Ham2<H_BURGERS2D>::value(p, q);
+      case H_NEGCOS2D: return Ham2<H_NEGCOS2D>::value(p, q, x, y);
+      case H_SIN2D: return Ham2<H_SIN2D>::value(p, q, x, y);
+      case H_EIKONAL2D: return Ham2<H_EIKONAL2D>::value(p, q, x, y);
+      default: return Ham2<H_BURGERS2D>::value(p, q, x, y);
     }
   }
-  __device__ __forceinline__ void alpha(float um, float up, float vm, float vp, float &ax, float &ay) const {
+  __device__ __forceinline__ void alpha(float um, float up, float vm, float vp, float x, float y, float &ax,
+                                        float &ay) const {
     switch (kind) {
-      case H_NEGCOS2D: Ham2<H_NEGCOS2D>::alpha(um, up, vm, vp, ax, ay); break;
-      case H_SIN2D: Ham2<H_SIN2D>::alpha(um, up, vm, vp, ax, ay); break;
-      case H_EIKONAL2D: Ham2<H_EIKONAL2D>::alpha(um, up, vm, vp, ax, ay); break;
-      default: Ham2<H_BURGERS2D>::alpha(um, up, vm, vp, ax, ay);
+      case H_NEGCOS2D: Ham2<H_NEGCOS2D>::alpha(um, up, vm, vp, x, y, ax, ay); break;
+      case H_SIN2D: Ham2<H_SIN2D>::alpha(um, up, vm, vp, x, y, ax, ay); break;
+      case H_EIKONAL2D: Ham2<H_EIKONAL2D>::alpha(um, up, vm, vp, x, y, ax, ay); break;
+      default: Ham2<H_BURGERS2D>::alpha(um, up, vm, vp, x, y, ax, ay);
     }
   }
 };
@@ -338,10 +365,11 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
       const int gi = tx0 + colY, gj = ty0 + y;
       const bool inside = !edge || (gi < nx && gj < ny);
       const float2 u = su[y * SUP + colY];
+      const float xn = fmaf((float)gi, d.dx, d.xlo), yn = fmaf((float)gj, d.dy, d.ylo);
       float ax, ay;
-      ham.alpha(u.x, u.y, dmq, dpq, ax, ay);
+      ham.alpha(u.x, u.y, dmq, dpq, xn, yn, ax, ay);
       const float aX = local_alpha ? ax : fax, aY = local_alpha ? ay : fay;
-      const float Hv = ham.value(0.5f * (u.y + u.x), 0.5f * (dpq + dmq));
+      const float Hv = ham.value(0.5f * (u.y + u.x), 0.5f * (dpq + dmq), xn, yn);
       const float L = fmaf(aX * 0.5f, u.y - u.x, fmaf(aY * 0.5f, dpq - dmq, -Hv));
       if (inside) {
         if (!isfinite(L)) bad = true;   // L depends on all four one-sided derivatives

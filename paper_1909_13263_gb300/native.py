@@ -27,8 +27,8 @@ STATUS = {0: "ALW_OK", 1: "ALW_EINVAL", 2: "ALW_ENOMEM", 3: "ALW_ECUDA", 4: "ALW
           5: "ALW_ETIMEOUT", 6: "ALW_EBUSY", 7: "ALW_EBUDGET", 8: "ALW_ENOTFOUND"}
 BC = {"periodic": 0, "linextrap": 1}
 HAM = {"burgers2d": 0, "negcos2d": 1, "sin2d": 2, "advect1d": 3, "burgers1d": 4, "negcos1d": 5,
-       "eikonal2d": 6, "nonconvex1d": 7}
-HAM_DIM = {"burgers2d": 2, "negcos2d": 2, "sin2d": 2, "eikonal2d": 2, "advect1d": 1, "burgers1d": 1,
+       "eikonal2d": 6, "nonconvex1d": 7, "optctrl2d": 8}
+HAM_DIM = {"burgers2d": 2, "negcos2d": 2, "sin2d": 2, "eikonal2d": 2, "optctrl2d": 2, "advect1d": 1, "burgers1d": 1,
            "negcos1d": 1, "nonconvex1d": 1}
 WEIGHTS = {"arclength": 0, "jp": 1}
 ALPHA = {"default": -1, "local_lagged": 0, "local_exact": 1, "global_lagged": 2, "global_exact": 3,

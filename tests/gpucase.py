@@ -47,7 +47,8 @@ class Case:
             am = "local_lagged" if self.dim == 1 else "global_lagged"
         return oracle.make_cfg(dim=self.dim, nx=self.nx, ny=self.ny, bc=self.bc, dx=self.dx, dy=self.dy,
                                ham=self.ham, weights=self.weights, eps=self.eps, dt_mode=self.dt_mode,
-                               alpha_mode=am, alpha_fixed=self.alpha_fixed)
+                               alpha_mode=am, alpha_fixed=self.alpha_fixed, xlo=self.lo,
+                               ylo=self.lo if self.dim == 2 else 0.0)
 
     def field(self, seed=0, kind="rough"):
         if self.dim == 1:

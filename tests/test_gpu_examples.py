@@ -1,10 +1,13 @@
-"""The CUDA path on Examples 5 and 8 of Sec. 3 at the paper's sizes (N = 100), FP64,
-against the oracle element by element and against the exact solution.
+"""The CUDA path on Examples 5, 8 and 11 of Sec. 3 at the paper's sizes, FP64,
+against the oracle element by element (and against exact solutions where known).
 
-Example 5: linear advection of a profile with corners, to t = 2 and t = 8.
-Example 8: the non-convex H = (p^2-1)(p^2-4)/4 from phi0 = -2|x| to t = 1, where
-the node alpha is the maximum of |H_p| over the interval between u^- and u^+.
+Example 5: linear advection of a profile with corners, N = 100, to t = 2 and t = 8.
+Example 8: the non-convex H = (p^2-1)(p^2-4)/4 from phi0 = -2|x| to t = 1, N = 100,
+where the node alpha is the maximum of |H_p| over the interval between u^- and u^+.
+Example 11: the optimal-control H(x, y, p, q) on [-pi, pi)^2 from phi0 = 0 to t = 1, 60^2.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -88,3 +91,27 @@ def test_example8_interval_alpha_stage_parity(precision):
         got1 = s.get_stage_phi(1)
     tol = FP64_TOL if precision == "fp64" else 64 * 2.0**-24
     assert rel_err(got1, ref1) <= tol
+
+
+@pytest.mark.parametrize("weights", ["arclength", "jp"])
+def test_example11_optimal_control_matches_oracle(weights):
+    n = 60
+    case = Case(2, n, n, "optctrl2d", weights=weights, lo=-math.pi, hi=math.pi, alpha_mode="default")
+    got, ref = _solve_both(case, np.zeros((n, n)), 1.0)
+    assert rel_err(got, ref) <= FP64_TOL
+    # the running cost is non-negative and phi0 = 0, so phi grows from 0 where the cost is positive
+    assert got.min() > -0.05 and got.max() > 0.5
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_example11_float_paths_track_fp64(precision):
+    # the position-dependent H in the float tile kernel (coordinates formed per node in float)
+    n = 96
+    out = {}
+    for prec in ("fp64", precision):
+        case = Case(2, n, n, "optctrl2d", lo=-math.pi, hi=math.pi, alpha_mode="default", precision=prec)
+        with case.solver() as s:
+            s.set_phi0(np.zeros((n, n)))
+            s.step_to(0.5)
+            out[prec] = s.get_phi()
+    assert np.max(np.abs(out[precision] - out["fp64"])) < 1e-4

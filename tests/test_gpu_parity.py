@@ -38,6 +38,8 @@ CASES_2D = [
     Case(2, 40, 40, "burgers2d", alpha_mode="fixed", alpha_fixed=(3.0, 2.5)),
     Case(2, 7, 5, "negcos2d"),
     Case(2, 3, 9, "burgers2d"),
+    Case(2, 45, 38, "optctrl2d", lo=-math.pi, hi=math.pi),
+    Case(2, 40, 33, "optctrl2d", lo=-math.pi, hi=math.pi, alpha_mode="local_lagged"),
 ]
 CASES_1D = [
     Case(1, 300, 1, "burgers1d", alpha_mode="local_lagged"),
@@ -108,6 +110,8 @@ def test_fp64_solve_matches_oracle(case):
     Case(2, 150, 70, "negcos2d", bc="linextrap"),
     Case(2, 65, 33, "sin2d", alpha_mode="local_lagged"),
     Case(1, 300, 1, "burgers1d", alpha_mode="local_lagged"),
+    Case(2, 130, 70, "optctrl2d", lo=-math.pi, hi=math.pi),
+    Case(2, 70, 66, "optctrl2d", lo=-math.pi, hi=math.pi, alpha_mode="local_lagged"),
 ], ids=_ids)
 def test_float_rk_stages_within_bound(case, weights, precision):
     case.weights, case.precision = weights, precision
