@@ -265,6 +265,8 @@ def bench_serving(args, stream, rate):
     with native.Server(hbm_budget_bytes=int(args.serve_budget_gb * 2**30), max_slots=256, max_side=2048,
                        weights=args.weights, stream=stream) as srv:
         srv.set_round_steps(args.serve_round_steps)
+        if args.serve_round_tiles is not None:
+            srv.set_round_tiles(args.serve_round_tiles)
         ids = [None] * len(reqs)
         t0 = time.perf_counter()
         for k, ((at, inst), ph) in enumerate(zip(reqs, phis)):
@@ -279,7 +281,9 @@ def bench_serving(args, stream, rate):
         makespan = time.perf_counter() - t0
         rounds = srv.stats()["rounds"]
     served = {"rate_per_s": rate, "requests": len(reqs), "solves_per_s": len(reqs) / makespan,
-              "rounds": rounds, "round_steps": args.serve_round_steps, **_latency_summary(lat)}
+              "rounds": rounds, "round_steps": args.serve_round_steps,
+              "round_tiles": "default" if args.serve_round_tiles is None else args.serve_round_tiles,
+              **_latency_summary(lat)}
     # one-at-a-time plain solves of the same arrivals (FIFO, a single worker)
     lat_s = []
     done_at = 0.0
@@ -539,6 +543,8 @@ def main():
     ap.add_argument("--serial-count", type=int, default=128)
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--serve-round-steps", type=int, default=4)
+    ap.add_argument("--serve-round-tiles", type=int, default=None,
+                    help="tile limit of a server round (default: the server's own, four kernel waves; 0: none)")
     ap.add_argument("--serve-rates", type=str, default="", help="comma-separated arrival rates (a sweep)")
     ap.add_argument("--report", choices=["", "precision"], default="",
                     help="precision: errors of the float paths against FP64 and the exact solution")

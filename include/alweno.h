@@ -276,6 +276,12 @@ alw_status alw_server_create(const alw_scheme *scheme, size_t hbm_budget_bytes, 
  * instance stretch to the fewest remaining steps among the active instances,
  * at most 16, so that a lone large solve is not slowed by round trips. */
 alw_status alw_server_set_round_steps(alw_server *s, int32_t steps);
+/* Round membership: the oldest resident instance always runs; the others join in
+ * admission order while the round holds at most `tiles` tiles (64 x 32 nodes each)
+ * in total, and instances of at most 32 tiles always join.  Large solves thus run
+ * in arrival order with the small ones beside them.  0 = no limit (every resident
+ * instance in every round).  Default: four waves of the persistent stage kernel. */
+alw_status alw_server_set_round_tiles(alw_server *s, int32_t tiles);
 /* Queue a solve (host_phi0 copied); req_id receives its id. */
 alw_status alw_server_submit(alw_server *s, const alw_grid *grid, const alw_hamiltonian *ham, const double *host_phi0,
                              size_t n, double t_final, uint64_t *req_id);

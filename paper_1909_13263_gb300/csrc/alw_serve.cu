@@ -103,8 +103,12 @@ struct Request {
   long long row_off = -1, rows = 0;
   int64_t steps = 0;
   int steps_cur = 0;  // MIXED: buffer pair holding the final phi
+  bool primed = false;  // first lagged alpha computed (on the instance's first round)
   double t_submit = 0, t_admit = 0, t_done = 0;
 };
+
+// Instances of at most this many tiles join every round whatever the tile limit.
+constexpr int kSmallTiles = 32;
 
 }  // namespace
 
@@ -116,6 +120,7 @@ struct alw_server {
   bool own_stream = false;
   size_t budget = 0;
   int max_slots = 0, max_side = 0, steps_per_round = 2;
+  int round_tiles = 0;  // tile limit of a round beyond its oldest instance (0: none)
   int pitch = 0;
   long long rows_total = 0;
   void *arr[6] = {};
@@ -368,23 +373,39 @@ void copier_main(alw_server *s) {
 void worker_main(alw_server *s) {
   cudaSetDevice(s->device);
   std::vector<int> list, new_tiles;
-  std::vector<Request *> active;
+  std::vector<Request *> active, round;  // active: in admission order
   for (;;) {
     std::vector<Request *> fresh;
-    int steps = 1;
+    int steps = 1, tile_limit = 0;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       s->cv.wait(lk, [&] { return s->stop || s->fatal || !active.empty() || !s->ready.empty(); });
       if (s->stop || s->fatal) return;
       fresh.swap(s->ready);
       steps = s->steps_per_round;
+      tile_limit = s->round_tiles;
     }
     for (Request *r : fresh) active.push_back(r);
+    // members of this round, oldest first: the oldest always; the others while the round's
+    // tiles stay within the limit, and small instances always.  Large solves then run in
+    // arrival order (as one at a time would), with the small ones beside them.
+    round.clear();
+    long long round_tiles = 0;
+    bool any_new = false;
+    for (Request *r : active) {
+      const int nt = s->h_inst[r->slot].ntiles;
+      if (round.empty() || tile_limit <= 0 || round_tiles + nt <= tile_limit || nt <= kSmallTiles) {
+        round.push_back(r);
+        round_tiles += nt;
+        any_new |= !r->primed;
+      }
+    }
     // round length: long enough to amortise the round trip, short enough that the first
-    // active instance to finish is retired promptly (its remaining steps, at most 16)
-    if (fresh.empty()) {
+    // member to finish is retired promptly (its remaining steps, at most 16); short while
+    // new instances are joining
+    if (!any_new) {
       double rem_min = 1e30;
-      for (Request *r : active) {
+      for (Request *r : round) {
         const DevState &ds = s->h_state[r->slot];
         if (ds.dt > 0.0) rem_min = std::min(rem_min, std::ceil((ds.t_final - ds.t) / ds.dt));
       }
@@ -392,12 +413,12 @@ void worker_main(alw_server *s) {
     }
     list.clear();
     new_tiles.clear();
-    for (Request *r : active) {
-      const bool is_new = std::find(fresh.begin(), fresh.end(), r) != fresh.end();
+    for (Request *r : round) {
       for (int t = 0; t < s->h_inst[r->slot].ntiles; ++t) {
         list.push_back(r->slot * 65536 + t);
-        if (is_new) new_tiles.push_back(r->slot * 65536 + t);
+        if (!r->primed) new_tiles.push_back(r->slot * 65536 + t);
       }
+      r->primed = true;
     }
     cudaError_t e = cudaSuccess;
     int le = 0;
@@ -535,9 +556,20 @@ alw_status alw_server_create(const alw_scheme *scheme, size_t hbm_budget_bytes, 
   s->stats.arena_rows = s->rows_total;
   if (cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
     return fail_destroy(serr(ALW_ECUDA, "stream creation failed"));
+  {  // default tile limit of a round: four waves of the persistent stage kernel
+    const int cap = s->prec == P_MIXED ? stage2d_grid_cap_mixed(scheme->weights) : stage2d_grid_cap_f32(scheme->weights);
+    s->round_tiles = 4 * std::max(cap, 1);
+  }
   s->worker = std::thread(worker_main, s);
   s->copier = std::thread(copier_main, s);
   *out = s;
+  return ALW_OK;
+}
+
+alw_status alw_server_set_round_tiles(alw_server *s, int32_t tiles) {
+  if (!s || tiles < 0) return serr(ALW_EINVAL, "the tile limit must be >= 0");
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->round_tiles = tiles;
   return ALW_OK;
 }
 

@@ -142,6 +142,7 @@ def load():
             "alw_batch_destroy": (ctypes.c_int, [P]),
             "alw_server_create": (ctypes.c_int, [ctypes.POINTER(Scheme), SZ, I32, I32, P, ctypes.POINTER(P)]),
             "alw_server_set_round_steps": (ctypes.c_int, [P, I32]),
+            "alw_server_set_round_tiles": (ctypes.c_int, [P, I32]),
             "alw_server_submit": (ctypes.c_int, [P, ctypes.POINTER(Grid), ctypes.POINTER(Hamiltonian), P, SZ, D,
                                                  ctypes.POINTER(ctypes.c_uint64)]),
             "alw_server_poll": (ctypes.c_int, [P, ctypes.c_uint64, D, ctypes.POINTER(I32), P, SZ,
@@ -416,6 +417,9 @@ class Server:
 
     def set_round_steps(self, steps: int):
         check(self._L.alw_server_set_round_steps(self._h, int(steps)))
+
+    def set_round_tiles(self, tiles: int):
+        check(self._L.alw_server_set_round_tiles(self._h, int(tiles)))
 
     def submit(self, *, nx: int, ny: int, xlo: float, xhi: float, ylo: float, yhi: float, ham: str, phi0,
                t_final: float) -> int:

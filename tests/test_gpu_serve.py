@@ -27,11 +27,16 @@ def _single(inst):
         return s.get_phi(), steps
 
 
-def test_served_results_equal_single_solves():
+@pytest.mark.parametrize("round_tiles", [None, 0, 60])
+def test_served_results_equal_single_solves(round_tiles):
+    # None: the default tile limit; 0: every resident instance in every round; 60: instances
+    # above 32 tiles (here up to 520^2 = 9 x 17 tiles) wait for their turn behind older ones
     insts = [inputs.Instance(i.n, i.ham, i.theta, i.t_final * 0.3)
-             for i in inputs.batch_instances(18, 24, 220, seed=77)]
-    with native.Server(hbm_budget_bytes=1 << 30, max_slots=6, max_side=256) as srv:
+             for i in inputs.batch_instances(18, 24, 520, seed=77)]
+    with native.Server(hbm_budget_bytes=1 << 30, max_slots=6, max_side=520) as srv:
         srv.set_round_steps(2)
+        if round_tiles is not None:
+            srv.set_round_tiles(round_tiles)
         ids = []
         for k, inst in enumerate(insts):
             phi0, _ = inputs.instance_phi0(inst)
