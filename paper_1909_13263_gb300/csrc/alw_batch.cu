@@ -166,6 +166,7 @@ Stage2DParams batch_params(const alw_batch *b, int stage, int loop_mode, int nti
     q.map_c = -1;
   }
   q.ntiles = ntiles;
+  q.grid_ctas = b->tuning.grid_ctas;
   q.insts = b->d_inst;
   q.tiles = b->d_tiles;
   q.done_count = b->d_done;
@@ -177,7 +178,7 @@ int launch(const alw_batch *b, const Stage2DParams &q) {
 }
 
 // Work list of the instances for which `live[i]` holds, in the requested order.
-std::vector<int> work_list(const alw_batch *b, const std::vector<char> &live, int order) {
+std::vector<int> ordered_list(const alw_batch *b, const std::vector<char> &live, int order) {
   std::vector<int> ids;
   for (size_t i = 0; i < b->h_inst.size(); ++i)
     if (live[i]) ids.push_back((int)i);
@@ -196,6 +197,16 @@ std::vector<int> work_list(const alw_batch *b, const std::vector<char> &live, in
       for (int t = 0; t < b->h_inst[i].ntiles; ++t) list.push_back(i * 65536 + t);
   }
   return list;
+}
+
+// The work list of the live instances in the given order and layout (ALW_LAYOUT_*), for the CTA
+// count the launches will use.
+std::vector<int> work_list(const alw_batch *b, const std::vector<char> &live, int order, int layout) {
+  std::vector<int> list = ordered_list(b, live, order);
+  if (layout != ALW_LAYOUT_CTA_RUNS) return list;
+  std::vector<int> out;
+  cta_runs(list, stage2d_grid((int)list.size(), b->tuning.grid_ctas, b->grid_cap), out);
+  return out;
 }
 
 alw_status upload_list(alw_batch *b, const std::vector<int> &list) {
@@ -373,12 +384,12 @@ alw_status build(alw_batch *b) {
   if (st) return st;
   for (auto &pd : b->pend) std::vector<double>().swap(pd.phi0);
   std::vector<char> live(n, 1);
-  st = upload_list(b, work_list(b, live, ALW_ORDER_INSTANCE));
+  b->grid_cap = cap_for(b);
+  st = upload_list(b, work_list(b, live, ALW_ORDER_INSTANCE, ALW_LAYOUT_CTA_RUNS));
   if (st) return st;
   st = prime_alpha(b, (int)total_tiles);
   if (st) return st;
   B_CUDA(cudaStreamSynchronize(b->stream));
-  b->grid_cap = cap_for(b);
   b->built = true;
   return ALW_OK;
 }
@@ -430,19 +441,23 @@ alw_status autotune(alw_batch *b) {
   alw_batch_tuning best{};
   double best_ms = 1e30;
   const int orders[3] = {ALW_ORDER_INSTANCE, ALW_ORDER_LARGEST_FIRST, ALW_ORDER_INTERLEAVED};
-  for (int o : orders) {
-    alw_status st = upload_list(b, work_list(b, live, o));
-    if (st) return st;
-    double ms;
-    st = trial(b, (int)total, 1, &ms);  // warm-up
-    if (st) return st;
-    st = trial(b, (int)total, 3, &ms);
-    if (st) return st;
-    if (ms < best_ms) {
-      best_ms = ms;
-      best.order = o;
+  const int layouts[2] = {ALW_LAYOUT_CTA_RUNS, ALW_LAYOUT_STRIDED};
+  b->tuning.grid_ctas = 0;
+  for (int o : orders)
+    for (int l : layouts) {
+      alw_status st = upload_list(b, work_list(b, live, o, l));
+      if (st) return st;
+      double ms;
+      st = trial(b, (int)total, 1, &ms);  // warm-up
+      if (st) return st;
+      st = trial(b, (int)total, 3, &ms);
+      if (st) return st;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best.order = o;
+        best.layout = l;
+      }
     }
-  }
   best.steps_per_graph = total >= 4096 ? 2 : (total >= 512 ? 8 : 32);
   best.grid_ctas = 0;  // occupancy cap
   b->tuning = best;
@@ -521,7 +536,8 @@ alw_status alw_batch_set_tuning(alw_batch *b, const alw_batch_tuning *t) {
     return ALW_OK;
   }
   if (t->order < ALW_ORDER_INSTANCE || t->order > ALW_ORDER_INTERLEAVED || t->steps_per_graph < 1 ||
-      t->steps_per_graph > 256 || t->grid_ctas < 0)
+      t->steps_per_graph > 256 || t->grid_ctas < 0 ||
+      (t->layout != ALW_LAYOUT_STRIDED && t->layout != ALW_LAYOUT_CTA_RUNS))
     return berr(ALW_EINVAL, "bad tuning");
   b->tuning = *t;
   b->user_tuning = true;
@@ -560,7 +576,7 @@ alw_status alw_batch_run(alw_batch *b, int64_t *replays_out) {
   int stalls = 0;
   long long last_steps_sum = -1;
   while (nlive > 0) {
-    std::vector<int> list = work_list(b, live, b->tuning.order);
+    std::vector<int> list = work_list(b, live, b->tuning.order, b->tuning.layout);
     st = upload_list(b, list);
     if (st) return st;
     st = build_graph(b, b->tuning.steps_per_graph, (int)list.size());

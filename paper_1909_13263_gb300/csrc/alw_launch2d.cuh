@@ -29,7 +29,7 @@ static int launch2d_one(const Stage2DParams &prm, cudaStream_t stream) {
   constexpr int NARR = (PREC == P_MIXED) ? 3 : 2;
   const int cap = grid_cap_of<PREC, W, H>();
   if (cap < 0) return (int)cudaGetLastError();
-  const int grid = prm.ntiles < cap ? prm.ntiles : cap;
+  const int grid = stage2d_grid(prm.ntiles, prm.grid_ctas, cap);
   if (grid <= 0) return 0;
   stage2d_kernel<PREC, W, H><<<grid, Geo2D::NT, Geo2D::smem_bytes<NARR>(), stream>>>(prm);
   return (int)cudaGetLastError();

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda.h>
 
+#include <vector>
+
 #include "alw_internal.h"
 
 namespace alw {
@@ -27,6 +29,7 @@ struct Stage2DParams {
   StageParams p;        // stage, modes, slots, pitch and buffers (per-instance fields unused in a batch)
   int map_a, map_b, map_c;  // FP32: source, base (-1: none); MIXED: hi base index, lo base index, delta (-1: none)
   int ntiles;               // work-list length
+  int grid_ctas;            // persistent CTAs to launch (0: as many as fit; never more than fit or ntiles)
   const InstDesc *insts;    // batch: instance table (nullptr: the single instance `inst0`)
   const int *tiles;         // batch: work list, entry = instance * 65536 + tile of that instance
   int *done_count;          // batch: incremented when an instance reaches its t_final (may be null)
@@ -36,6 +39,28 @@ struct Stage2DParams {
 // TMA box of one tile with its halo (floats): 72 columns x 38 rows.
 constexpr int kBox2DW = 72, kBox2DH = 38;
 constexpr int kTile2DX = 64, kTile2DY = 32;
+
+// CTAs a launch of `ntiles` work-list entries uses: min(ntiles, grid_ctas or cap, cap).
+inline int stage2d_grid(int ntiles, int grid_ctas, int cap) {
+  int g = (grid_ctas > 0 && grid_ctas < cap) ? grid_ctas : cap;
+  return ntiles < g ? ntiles : g;
+}
+
+// The persistent kernel hands CTA c the work-list entries c, c + G, c + 2G, ...  Reorders an
+// instance-major list so that each CTA's entries form one contiguous stretch of it: a CTA then
+// meets few instance boundaries (each closes a run: alpha fold, counter atomics, a fence) and
+// walks neighbouring tiles of one instance in turn.
+inline void cta_runs(const std::vector<int> &in, int G, std::vector<int> &out) {
+  const int n = (int)in.size();
+  out.resize(n);
+  if (G <= 0 || n == 0) return;
+  int start = 0;
+  for (int c = 0; c < G && c < n; ++c) {
+    const int cnt = (n - c + G - 1) / G;  // entries c, c + G, ... below n
+    for (int k = 0; k < cnt; ++k) out[c + k * G] = in[start + k];
+    start += cnt;
+  }
+}
 
 int launch_stage2d_f32(const Stage2DParams &prm, void *stream);
 int launch_stage2d_mixed(const Stage2DParams &prm, void *stream);

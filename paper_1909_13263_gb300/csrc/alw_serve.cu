@@ -121,6 +121,7 @@ struct alw_server {
   size_t budget = 0;
   int max_slots = 0, max_side = 0, steps_per_round = 2;
   int round_tiles = 0;  // tile limit of a round beyond its oldest instance (0: none)
+  int grid_cap = 1;     // CTAs of the persistent stage kernel that fit on the device
   int pitch = 0;
   long long rows_total = 0;
   void *arr[6] = {};
@@ -372,7 +373,7 @@ void copier_main(alw_server *s) {
 // Compute thread: rounds of RK steps over every active instance.
 void worker_main(alw_server *s) {
   cudaSetDevice(s->device);
-  std::vector<int> list, new_tiles;
+  std::vector<int> list, new_tiles, tmp;
   std::vector<Request *> active, round;  // active: in admission order
   for (;;) {
     std::vector<Request *> fresh;
@@ -420,6 +421,11 @@ void worker_main(alw_server *s) {
       }
       r->primed = true;
     }
+    // each persistent CTA takes one contiguous stretch of the instance-major lists
+    cta_runs(list, stage2d_grid((int)list.size(), 0, s->grid_cap), tmp);
+    list.swap(tmp);
+    cta_runs(new_tiles, stage2d_grid((int)new_tiles.size(), 0, s->grid_cap), tmp);
+    new_tiles.swap(tmp);
     cudaError_t e = cudaSuccess;
     int le = 0;
     if (!new_tiles.empty()) {  // first lagged alpha of the new instances
@@ -558,7 +564,8 @@ alw_status alw_server_create(const alw_scheme *scheme, size_t hbm_budget_bytes, 
     return fail_destroy(serr(ALW_ECUDA, "stream creation failed"));
   {  // default tile limit of a round: four waves of the persistent stage kernel
     const int cap = s->prec == P_MIXED ? stage2d_grid_cap_mixed(scheme->weights) : stage2d_grid_cap_f32(scheme->weights);
-    s->round_tiles = 4 * std::max(cap, 1);
+    s->grid_cap = std::max(cap, 1);
+    s->round_tiles = 4 * s->grid_cap;
   }
   s->worker = std::thread(worker_main, s);
   s->copier = std::thread(copier_main, s);
