@@ -108,6 +108,7 @@ struct alw_batch {
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0, graph_ntiles = 0;
   int grid_cap = 0;
+  int kind1 = 0;  // 1 + the Hamiltonian every instance of the current work list shares (0: mixed)
 
   void *alloc(size_t bytes) {
     void *p = dev_alloc(bytes, stream);
@@ -167,6 +168,7 @@ Stage2DParams batch_params(const alw_batch *b, int stage, int loop_mode, int nti
   }
   q.ntiles = ntiles;
   q.grid_ctas = b->tuning.grid_ctas;
+  q.batch_kind1 = b->kind1;
   q.insts = b->d_inst;
   q.tiles = b->d_tiles;
   q.done_count = b->d_done;
@@ -201,7 +203,15 @@ std::vector<int> ordered_list(const alw_batch *b, const std::vector<char> &live,
 
 // The work list of the live instances in the given order and layout (ALW_LAYOUT_*), for the CTA
 // count the launches will use.
-std::vector<int> work_list(const alw_batch *b, const std::vector<char> &live, int order, int layout) {
+std::vector<int> work_list(alw_batch *b, const std::vector<char> &live, int order, int layout) {
+  int kind = -1;
+  bool uniform = true;
+  for (size_t i = 0; i < b->h_inst.size(); ++i) {
+    if (!live[i]) continue;
+    if (kind < 0) kind = b->h_inst[i].ham;
+    uniform = uniform && b->h_inst[i].ham == kind;
+  }
+  b->kind1 = (uniform && kind >= 0) ? kind + 1 : 0;  // launches of this list use that kernel
   std::vector<int> list = ordered_list(b, live, order);
   if (layout != ALW_LAYOUT_CTA_RUNS) return list;
   std::vector<int> out;

@@ -37,7 +37,16 @@ static int launch2d_one(const Stage2DParams &prm, cudaStream_t stream) {
 
 template <int PREC, int W>
 static int launch2d_h(const Stage2DParams &prm, cudaStream_t s) {
-  if (prm.insts) return launch2d_one<PREC, W, -1>(prm, s);
+  if (prm.insts) {
+    // a batch whose instances share one Hamiltonian runs that Hamiltonian's own kernel
+    switch (prm.batch_kind1 - 1) {
+      case H_BURGERS2D: return launch2d_one<PREC, W, H_BURGERS2D>(prm, s);
+      case H_NEGCOS2D: return launch2d_one<PREC, W, H_NEGCOS2D>(prm, s);
+      case H_SIN2D: return launch2d_one<PREC, W, H_SIN2D>(prm, s);
+      case H_EIKONAL2D: return launch2d_one<PREC, W, H_EIKONAL2D>(prm, s);
+      default: return launch2d_one<PREC, W, -1>(prm, s);
+    }
+  }
   switch (prm.inst0.ham) {
     case H_BURGERS2D: return launch2d_one<PREC, W, H_BURGERS2D>(prm, s);
     case H_NEGCOS2D: return launch2d_one<PREC, W, H_NEGCOS2D>(prm, s);

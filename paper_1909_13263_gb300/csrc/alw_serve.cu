@@ -122,6 +122,7 @@ struct alw_server {
   int max_slots = 0, max_side = 0, steps_per_round = 2;
   int round_tiles = 0;  // tile limit of a round beyond its oldest instance (0: none)
   int grid_cap = 1;     // CTAs of the persistent stage kernel that fit on the device
+  int kind1 = 0;        // 1 + the Hamiltonian all members of the current round share (0: mixed)
   int pitch = 0;
   long long rows_total = 0;
   void *arr[6] = {};
@@ -199,6 +200,7 @@ Stage2DParams server_params(const alw_server *s, int stage, int loop_mode, int n
     q.map_c = -1;
   }
   q.ntiles = ntiles;
+  q.batch_kind1 = s->kind1;
   q.insts = s->d_inst;
   q.tiles = s->d_tiles;
   q.done_count = nullptr;
@@ -422,6 +424,11 @@ void worker_main(alw_server *s) {
       r->primed = true;
     }
     // each persistent CTA takes one contiguous stretch of the instance-major lists
+    // a round whose members share one Hamiltonian runs that Hamiltonian's own kernel
+    int kind1 = round.empty() ? 0 : round.front()->ham + 1;
+    for (Request *r : round)
+      if (r->ham + 1 != kind1) kind1 = 0;
+    s->kind1 = kind1;
     cta_runs(list, stage2d_grid((int)list.size(), 0, s->grid_cap), tmp);
     list.swap(tmp);
     cta_runs(new_tiles, stage2d_grid((int)new_tiles.size(), 0, s->grid_cap), tmp);

@@ -32,10 +32,14 @@ def _single(inst, precision, weights):
         return s.get_phi(), steps
 
 
-@pytest.mark.parametrize("precision,weights", [("mixed", "arclength"), ("fp32", "jp"), ("mixed", "jp")])
-def test_batch_equals_single_solves(precision, weights):
+@pytest.mark.parametrize("precision,weights,uniform", [("mixed", "arclength", False), ("fp32", "jp", False),
+                                                       ("mixed", "jp", False), ("mixed", "arclength", True)])
+def test_batch_equals_single_solves(precision, weights, uniform):
+    # uniform: every instance has the same Hamiltonian, so the batch runs that Hamiltonian's kernel
     insts = _mix(10, 24, 200, seed=11)
     insts.append(inputs.Instance(65, "negcos2d", 1.0, 0.3 / math.pi**2 * 0.25))   # ragged tiles
+    if uniform:
+        insts = [inputs.Instance(i.n, "negcos2d", i.theta, i.t_final) for i in insts]
     with native.Batch(precision=precision, weights=weights) as b:
         for inst in insts:
             phi0, _ = inputs.instance_phi0(inst)
