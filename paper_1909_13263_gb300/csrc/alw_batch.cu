@@ -170,6 +170,7 @@ Stage2DParams batch_params(const alw_batch *b, int stage, int loop_mode, int nti
   q.grid_ctas = b->tuning.grid_ctas;
   q.batch_kind1 = b->kind1;
   q.insts = b->d_inst;
+  q.states = b->d_state;
   q.tiles = b->d_tiles;
   q.done_count = b->d_done;
   return q;

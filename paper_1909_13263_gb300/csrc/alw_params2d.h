@@ -32,6 +32,7 @@ struct Stage2DParams {
   int grid_ctas;            // persistent CTAs to launch (0: as many as fit; never more than fit or ntiles)
   int batch_kind1;          // batch: 1 + the Hamiltonian all listed instances share (0: they differ)
   const InstDesc *insts;    // batch: instance table (nullptr: the single instance `inst0`)
+  DevState *states;         // batch: state of instance i at states + i (nullptr: read insts[i].st)
   const int *tiles;         // batch: work list, entry = instance * 65536 + tile of that instance
   int *done_count;          // batch: incremented when an instance reaches its t_final (may be null)
   InstDesc inst0;

@@ -201,6 +201,7 @@ Stage2DParams server_params(const alw_server *s, int stage, int loop_mode, int n
   }
   q.ntiles = ntiles;
   q.batch_kind1 = s->kind1;
+  q.states = s->d_state;
   q.insts = s->d_inst;
   q.tiles = s->d_tiles;
   q.done_count = nullptr;

@@ -137,10 +137,16 @@ struct Geo2D {
 static_assert(Geo2D::SW == kBox2DW && Geo2D::SH == kBox2DH, "TMA box must match the tile halo");
 
 // Per-tile values prepared by thread 0 when the tile's loads are issued.
+// Everything a tile needs from its instance, gathered by thread 0 into shared memory when the
+// tile is prepared (one tile ahead), so that the compute phase reads no instance data from
+// global memory.
 struct TileInfo {
   int inst, tx0, ty0, cur, skip, last;
   float dtf, fax, fay;
   double dt;
+  int nx, ny, row_off, bc, ham, ntiles, tiles_x;
+  float dx, dy, rdx, rdy, xlo, ylo;
+  DevState *st;
 };
 
 template <int PREC, int W, int H>
@@ -178,7 +184,7 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
   auto desc = [&](int inst) -> const InstDesc & { return batch ? prm.insts[inst] : prm.inst0; };
 
   // thread 0: one TMA box per array of the tile (with halo) into buffer b
-  auto issue_loads = [&](const TileInfo &info, const InstDesc &d, int b) {
+  auto issue_loads = [&](const TileInfo &info, int b) {
     const CUtensorMap *mA, *mB = nullptr, *mC = nullptr;
     if (PREC == P_MIXED) {
       mA = &prm.maps[prm.map_a + info.cur];
@@ -190,39 +196,56 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
     }
     const int nm = 1 + (mB != nullptr) + (mC != nullptr);
     float *dst = raw + b * NARR * ARR;
-    const int y = d.row_off + info.ty0;
+    const int y = info.row_off + info.ty0;
     mbar_arrive_expect_tx(&bars[b], box_bytes * nm);
     tma_load_2d(dst, mA, info.tx0, y, &bars[b]);
     if (mB) tma_load_2d(dst + ARR, mB, info.tx0, y, &bars[b]);
     if (mC) tma_load_2d(dst + 2 * ARR, mC, info.tx0, y, &bars[b]);
   };
 
-  // thread 0: decode work-list entry t, compute its instance's stage scalars (reused while the
-  // instance repeats), issue its loads into buffer b
-  auto prepare = [&](int t, int b) {
+  // thread 0: decode work-list entry e (of list position t), gather its instance's fields and
+  // stage scalars (reused while the instance repeats), issue its loads into buffer b
+  auto prepare = [&](int t, int e, int b) {
     int inst = 0, tl = t;
     if (batch) {
-      const int e = prm.tiles[t];
       inst = e >> 16;
       tl = e & 0xffff;
     }
-    const InstDesc &d = desc(inst);
-    const DevState *st = d.st;
     TileInfo info;
     if (inst == s_pinfo.inst) {
       info = s_pinfo;
-      info.tx0 = (tl % d.tiles_x) * TX;
-      info.ty0 = (tl / d.tiles_x) * TY;
+      info.tx0 = (tl % info.tiles_x) * TX;
+      info.ty0 = (tl / info.tiles_x) * TY;
       s_info[b] = info;
       s_pinfo = info;
-      if (!info.skip) issue_loads(info, d, b);
+      if (!info.skip) issue_loads(info, b);
       return;
     }
+    // the instance's descriptor and its state (contiguous states: no dependent load)
+    const InstDesc &d = desc(inst);
+    DevState *st = (batch && prm.states) ? prm.states + inst : d.st;
     info.inst = inst;
-    info.tx0 = (tl % d.tiles_x) * TX;
-    info.ty0 = (tl / d.tiles_x) * TY;
-    info.cur = (PREC == P_MIXED) ? st->cur : 0;
-    info.skip = (st->err != 0) || (p.loop_mode == LOOP_STEP_TO && !(st->t < st->t_final));
+    info.nx = d.nx;
+    info.ny = d.ny;
+    info.row_off = d.row_off;
+    info.bc = d.bc;
+    info.ham = d.ham;
+    info.ntiles = d.ntiles;
+    info.tiles_x = d.tiles_x;
+    info.dx = d.dx;
+    info.dy = d.dy;
+    info.rdx = d.rdx;
+    info.rdy = d.rdy;
+    info.xlo = d.xlo;
+    info.ylo = d.ylo;
+    info.st = st;
+    const double lx = d.lx, ly = d.ly;
+    const int s_cur = st->cur, s_err = st->err;
+    const double s_t = st->t, s_tf = st->t_final, s_dt = st->dt;
+    info.tx0 = (tl % info.tiles_x) * TX;
+    info.ty0 = (tl / info.tiles_x) * TY;
+    info.cur = (PREC == P_MIXED) ? s_cur : 0;
+    info.skip = (s_err != 0) || (p.loop_mode == LOOP_STEP_TO && !(s_t < s_tf));
     double dt;
     int last = 0;
     if (p.stage == 1 && p.loop_mode != LOOP_STAGE) {
@@ -234,16 +257,16 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
         ax = bits_to_double(st->alpha_bits[p.dt_slot][0]);
         ay = bits_to_double(st->alpha_bits[p.dt_slot][1]);
       }
-      const double den = ax / d.lx + ay / d.ly;
+      const double den = ax / lx + ay / ly;
       dt = den > 0.0 ? p.cfl / den : (p.loop_mode == LOOP_ADVANCE ? 0.0 : INFINITY);
-      if (p.loop_mode == LOOP_STEP_TO && st->t + dt >= st->t_final) {
-        dt = st->t_final - st->t;
+      if (p.loop_mode == LOOP_STEP_TO && s_t + dt >= s_tf) {
+        dt = s_tf - s_t;
         last = 1;
       }
     } else if (p.loop_mode == LOOP_STAGE) {
       dt = p.dt_value;
     } else {
-      dt = st->dt;
+      dt = s_dt;
     }
     info.dt = dt;
     info.dtf = (float)dt;
@@ -260,7 +283,7 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
     info.fay = fay;
     s_info[b] = info;
     s_pinfo = info;
-    if (!info.skip) issue_loads(info, d, b);
+    if (!info.skip) issue_loads(info, b);
   };
 
   if (tid == 0) {
@@ -268,7 +291,7 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
     mbar_init(&bars[1], 1);
     fence_mbar_init();
     s_pinfo.inst = -1;
-    if ((int)blockIdx.x < ntiles) prepare(blockIdx.x, 0);
+    if ((int)blockIdx.x < ntiles) prepare(blockIdx.x, batch ? prm.tiles[blockIdx.x] : 0, 0);
   }
   __syncthreads();
 
@@ -278,12 +301,16 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
   float amx = 0.0f, amy = 0.0f;
   bool bad = false;
   int run_tiles = 0;
+  // thread 0: work-list entry of the tile after next, loaded one tile ahead of its use
+  int e_ahead = (batch && tid == 0 && (int)(blockIdx.x + gridDim.x) < ntiles) ? prm.tiles[blockIdx.x + gridDim.x] : 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
     const int buf = k & 1;
     const int next = t + gridDim.x;
     if (tid == 0 && next < ntiles) {
       fence_proxy_async_smem();
-      prepare(next, buf ^ 1);
+      prepare(next, e_ahead, buf ^ 1);
+      const int after = next + (int)gridDim.x;
+      e_ahead = (batch && after < ntiles) ? prm.tiles[after] : 0;
     }
     const int i_inst = s_info[buf].inst, i_skip = s_info[buf].skip, i_cur = s_info[buf].cur;
     if (i_skip) {
@@ -294,7 +321,7 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
     if (__syncthreads_or(!ok)) {
       // a tile load never completed: flag the instance, let the other in-flight load land, stop
       if (tid == 0) {
-        atomicOr(&desc(i_inst).st->err, 2);
+        atomicOr(&s_info[buf].st->err, 2);
         if (next < ntiles && !s_info[buf ^ 1].skip) mbar_wait_bounded(&bars[buf ^ 1], (phase >> (buf ^ 1)) & 1u);
       }
       __syncthreads();
@@ -302,8 +329,8 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
     }
     phase ^= 1u << buf;
 
-    const InstDesc &d = desc(i_inst);
-    const int nx = d.nx, ny = d.ny, tx0 = s_info[buf].tx0, ty0 = s_info[buf].ty0;
+    const TileInfo &d = s_info[buf];  // this tile's instance fields (shared memory)
+    const int nx = d.nx, ny = d.ny, tx0 = d.tx0, ty0 = d.ty0;
     const size_t rbase = (size_t)d.row_off * p.pitch;   // element offset of the instance's rows
     const HamSel<H> ham{d.ham};
     const float dtf = s_info[buf].dtf, fax = s_info[buf].fax, fay = s_info[buf].fay;
