@@ -242,6 +242,10 @@ alw_status alw_batch_add(alw_batch *b, const alw_grid *grid, const alw_hamiltoni
 /* Fix the tuning (NULL: let the autotuner choose on the next run). */
 alw_status alw_batch_set_tuning(alw_batch *b, const alw_batch_tuning *tuning);
 alw_status alw_batch_get_tuning(alw_batch *b, alw_batch_tuning *tuning);
+/* Lay out the device arena, upload every instance and tune the work list now
+ * (alw_batch_run does this on its first call); instances cannot be added
+ * afterwards.  Separates set-up from the time loop. */
+alw_status alw_batch_build(alw_batch *b);
 /* Advance every instance to its t_final; returns after all have arrived.
  * replays_out (nullable): graph replays used.  ALW_ENONFINITE if an instance
  * saw a non-finite dH/dp (the others still finish). */

@@ -347,16 +347,21 @@ alw_status build(alw_batch *b) {
     const int r = encode_tile_map(&b->maps[i], bases[i], pitch, rows);
     if (r) return berr(ALW_ECUDA, "cuTensorMapEncodeTiled failed (%d)", r);
   }
-  // upload phi0 of every instance into its block of rows
-  size_t max_n = 0;
-  for (auto &pd : b->pend) max_n = std::max(max_n, pd.phi0.size());
-  void *tmp = dev_alloc(max_n * sizeof(double), b->stream);
-  if (!tmp) return berr(ALW_ENOMEM, "device allocation failed");
+  // upload phi0 of every instance into its block of rows: all instances are staged in one device
+  // buffer (copies queued back to back), then split into the arena with its ghost frame, with
+  // a single synchronisation at the end
+  size_t total_n = 0;
+  for (auto &pd : b->pend) total_n += pd.phi0.size();
+  double *stage = (double *)dev_alloc(total_n * sizeof(double), b->stream);
+  if (!stage) return berr(ALW_ENOMEM, "device allocation of %zu bytes failed", total_n * sizeof(double));
   alw_status st = ALW_OK;
+  size_t off_n = 0;
   for (int i = 0; i < n && st == ALW_OK; ++i) {
     const InstDesc &d = b->h_inst[i];
     const size_t off = (size_t)d.row_off * pitch;  // element offset of the instance's first row
-    cudaError_t e = cudaMemcpyAsync(tmp, b->pend[i].phi0.data(), b->pend[i].phi0.size() * sizeof(double),
+    double *src = stage + off_n;
+    off_n += b->pend[i].phi0.size();
+    cudaError_t e = cudaMemcpyAsync(src, b->pend[i].phi0.data(), b->pend[i].phi0.size() * sizeof(double),
                                     cudaMemcpyHostToDevice, b->stream);
     if (e != cudaSuccess) {
       st = berr(ALW_ECUDA, "upload: %s", cudaGetErrorString(e));
@@ -364,10 +369,9 @@ alw_status build(alw_batch *b) {
     }
     int le;
     if (b->prec == P_MIXED)
-      le = launch_mixed_split((const double *)tmp, (float *)b->H[0] + off, (float *)b->Lo[0] + off, d.nx, d.ny, pitch, 2,
-                              b->stream);
+      le = launch_mixed_split(src, (float *)b->H[0] + off, (float *)b->Lo[0] + off, d.nx, d.ny, pitch, 2, b->stream);
     else
-      le = launch_unpack(tmp, 0, (float *)b->P + off, 1, d.nx, d.ny, pitch, 2, b->stream);
+      le = launch_unpack(src, 0, (float *)b->P + off, 1, d.nx, d.ny, pitch, 2, b->stream);
     if (le) {
       st = berr(ALW_ECUDA, "upload kernel: %s", cudaGetErrorString((cudaError_t)le));
       break;
@@ -389,9 +393,9 @@ alw_status build(alw_batch *b) {
     }
     le = launch_ghosts(g, b->stream);
     if (le) st = berr(ALW_ECUDA, "ghost kernel: %s", cudaGetErrorString((cudaError_t)le));
-    cudaStreamSynchronize(b->stream);  // tmp is reused by the next instance
   }
-  dev_free(tmp, max_n * sizeof(double), b->stream);
+  cudaStreamSynchronize(b->stream);  // the staging buffer is released only after its readers
+  dev_free(stage, total_n * sizeof(double), b->stream);
   if (st) return st;
   for (auto &pd : b->pend) std::vector<double>().swap(pd.phi0);
   std::vector<char> live(n, 1);
@@ -559,6 +563,16 @@ alw_status alw_batch_set_tuning(alw_batch *b, const alw_batch_tuning *t) {
 alw_status alw_batch_get_tuning(alw_batch *b, alw_batch_tuning *t) {
   if (!b || !t) return berr(ALW_EINVAL, "NULL argument");
   *t = b->tuning;
+  return ALW_OK;
+}
+
+alw_status alw_batch_build(alw_batch *b) {
+  if (!b) return berr(ALW_EINVAL, "NULL argument");
+  if (!b->built) {
+    alw_status st = build(b);
+    if (st) return st;
+  }
+  if (!b->tuned) return autotune(b);
   return ALW_OK;
 }
 

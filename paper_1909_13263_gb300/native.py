@@ -137,6 +137,7 @@ def load():
                                              ctypes.POINTER(I32)]),
             "alw_batch_set_tuning": (ctypes.c_int, [P, ctypes.POINTER(BatchTuning)]),
             "alw_batch_get_tuning": (ctypes.c_int, [P, ctypes.POINTER(BatchTuning)]),
+            "alw_batch_build": (ctypes.c_int, [P]),
             "alw_batch_run": (ctypes.c_int, [P, ctypes.POINTER(I64)]),
             "alw_batch_get_phi": (ctypes.c_int, [P, I32, P, SZ]),
             "alw_batch_get_state": (ctypes.c_int, [P, I32, ctypes.POINTER(State)]),
@@ -365,6 +366,10 @@ class Batch:
         linv = {v: k for k, v in LAYOUT.items()}
         return {"order": inv.get(t.order, t.order), "steps_per_graph": t.steps_per_graph, "grid_ctas": t.grid_ctas,
                 "layout": linv.get(t.layout, t.layout)}
+
+    def build(self):
+        """Upload the instances and tune the work list now (run() does it on first use)."""
+        check(self._L.alw_batch_build(self._h))
 
     def run(self) -> int:
         r = ctypes.c_int64()
