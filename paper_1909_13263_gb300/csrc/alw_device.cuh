@@ -323,10 +323,21 @@ __device__ __noinline__ void store_ghosts(S *arr, int pitch, int nx, int ny, int
 template <typename S, int DIM>
 __device__ __forceinline__ void store_node(S *arr, int pitch, int nx, int ny, int bc, int gi, int gj, S val) {
   const int gy = (DIM == 2) ? GY : 0;
-  arr[(size_t)(gj + gy) * pitch + gi + GX] = val;
+  S *row = arr + (size_t)(gj + gy) * pitch;
+  row[gi + GX] = val;
   if (bc != BC_PERIODIC) return;
-  if (gi < 3 || gi >= nx - 3 || (DIM == 2 && (gj < 3 || gj >= ny - 3)))
-    store_ghosts<S, DIM>(arr, pitch, nx, ny, gi, gj, val);
+  if (nx >= 3 && (DIM == 1 || ny >= 3)) {
+    // with at least 3 nodes per direction a node is the periodic image of at most one ghost on
+    // each side: left ghost gi - nx for the last three nodes, right ghost gi + nx for the first three
+    if (gi >= nx - 3) row[gi - nx + GX] = val;
+    if (gi < 3) row[gi + nx + GX] = val;
+    if (DIM == 2) {
+      if (gj >= ny - 3) arr[(size_t)(gj - ny + GY) * pitch + gi + GX] = val;
+      if (gj < 3) arr[(size_t)(gj + ny + GY) * pitch + gi + GX] = val;
+    }
+  } else if (gi < 3 || gi >= nx - 3 || (DIM == 2 && (gj < 3 || gj >= ny - 3))) {
+    store_ghosts<S, DIM>(arr, pitch, nx, ny, gi, gj, val);  // tiny grids: several images per node
+  }
 }
 
 }  // namespace alw
