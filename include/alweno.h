@@ -224,7 +224,8 @@ enum { ALW_ORDER_INSTANCE = 0, ALW_ORDER_LARGEST_FIRST = 1, ALW_ORDER_INTERLEAVE
  * entries c, c+G, c+2G, ...): STRIDED uses the ordered list as it is, so
  * consecutive entries run side by side on neighbouring CTAs; CTA_RUNS reorders
  * it so that each CTA takes one contiguous stretch of the ordered list (few
- * instance boundaries per CTA when instances are small). */
+ * instance boundaries per CTA when instances are small).  The autotuner keeps
+ * STRIDED, which measures faster in full stages; CTA_RUNS is a fixed choice. */
 enum { ALW_LAYOUT_STRIDED = 0, ALW_LAYOUT_CTA_RUNS = 1 };
 
 typedef struct {

@@ -400,7 +400,7 @@ alw_status build(alw_batch *b) {
   for (auto &pd : b->pend) std::vector<double>().swap(pd.phi0);
   std::vector<char> live(n, 1);
   b->grid_cap = cap_for(b);
-  st = upload_list(b, work_list(b, live, ALW_ORDER_INSTANCE, ALW_LAYOUT_CTA_RUNS));
+  st = upload_list(b, work_list(b, live, ALW_ORDER_INSTANCE, ALW_LAYOUT_STRIDED));
   if (st) return st;
   st = prime_alpha(b, (int)total_tiles);
   if (st) return st;
@@ -456,7 +456,10 @@ alw_status autotune(alw_batch *b) {
   alw_batch_tuning best{};
   double best_ms = 1e30;
   const int orders[3] = {ALW_ORDER_INSTANCE, ALW_ORDER_LARGEST_FIRST, ALW_ORDER_INTERLEAVED};
-  const int layouts[2] = {ALW_LAYOUT_CTA_RUNS, ALW_LAYOUT_STRIDED};
+  // layouts: CTA runs time faster in these reduction-only trials (they make the per-run
+  // epilogue rare) but slower in full stages (neighbouring tiles no longer run side by side),
+  // so the autotuner keeps the strided layout; CTA runs stay available as a fixed tuning
+  const int layouts[1] = {ALW_LAYOUT_STRIDED};
   b->tuning.grid_ctas = 0;
   for (int o : orders)
     for (int l : layouts) {

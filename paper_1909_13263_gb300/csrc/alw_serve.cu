@@ -376,7 +376,7 @@ void copier_main(alw_server *s) {
 // Compute thread: rounds of RK steps over every active instance.
 void worker_main(alw_server *s) {
   cudaSetDevice(s->device);
-  std::vector<int> list, new_tiles, tmp;
+  std::vector<int> list, new_tiles;
   std::vector<Request *> active, round;  // active: in admission order
   for (;;) {
     std::vector<Request *> fresh;
@@ -424,16 +424,11 @@ void worker_main(alw_server *s) {
       }
       r->primed = true;
     }
-    // each persistent CTA takes one contiguous stretch of the instance-major lists
     // a round whose members share one Hamiltonian runs that Hamiltonian's own kernel
     int kind1 = round.empty() ? 0 : round.front()->ham + 1;
     for (Request *r : round)
       if (r->ham + 1 != kind1) kind1 = 0;
     s->kind1 = kind1;
-    cta_runs(list, stage2d_grid((int)list.size(), 0, s->grid_cap), tmp);
-    list.swap(tmp);
-    cta_runs(new_tiles, stage2d_grid((int)new_tiles.size(), 0, s->grid_cap), tmp);
-    new_tiles.swap(tmp);
     cudaError_t e = cudaSuccess;
     int le = 0;
     if (!new_tiles.empty()) {  // first lagged alpha of the new instances

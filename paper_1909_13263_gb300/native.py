@@ -352,7 +352,7 @@ class Batch:
         self.shapes.append((ny, nx))
         return i.value
 
-    def set_tuning(self, order: str = None, steps_per_graph: int = 4, grid_ctas: int = 0, layout: str = "cta_runs"):
+    def set_tuning(self, order: str = None, steps_per_graph: int = 4, grid_ctas: int = 0, layout: str = "strided"):
         if order is None:
             check(self._L.alw_batch_set_tuning(self._h, None))
             return
