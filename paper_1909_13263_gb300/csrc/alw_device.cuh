@@ -44,17 +44,22 @@ enum { A_LOCAL_LAGGED = 0, A_LOCAL_EXACT = 1, A_GLOBAL_LAGGED = 2, A_GLOBAL_EXAC
 template <typename T> struct Arith;
 
 template <> struct Arith<double> {
-  // F(u) and s = sqrt(1+u^2)
+  // F(u) = u s + asinh(u) and s = sqrt(1+u^2), with asinh|u| = log(|u| + s) reusing s.  F only
+  // enters divided differences (F(b) - F(a)) / (b - a) over intervals longer than 1e-3 s, so
+  // its absolute error is what counts: log of the rounded |u| + s >= 1 errs by about one unit
+  // of 1, like a correctly rounded F of size one.
   __device__ __forceinline__ static void F(double u, double &Fu, double &s) {
     s = sqrt(fma(u, u, 1.0));
-    Fu = fma(u, s, asinh(u));
+    Fu = fma(u, s, copysign(log(fabs(u) + s), u));
   }
-  // mean of sqrt(1+u^2) over [a, b]; near a == b the divided difference is
-  // 0/0, so its Taylor series about the midpoint is summed instead.
-  __device__ __forceinline__ static double G(double a, double Fa, double, double b, double Fb, double) {
-    const double h = b - a, m = 0.5 * (a + b);
+  // mean of sqrt(1+u^2) over [a, b]; near a == b the divided difference is 0/0, so its Taylor
+  // series about the midpoint is summed instead (below 1e-3 of the mean of the end values
+  // sa, sb, which bounds sqrt(1 + m^2) from above; both forms are accurate near the switch).
+  __device__ __forceinline__ static double G(double a, double Fa, double sa, double b, double Fb, double sb) {
+    const double h = b - a;
+    if (fabs(h) > 5e-4 * (sa + sb)) return (Fb - Fa) / (2.0 * h);
+    const double m = 0.5 * (a + b);
     const double s2 = fma(m, m, 1.0), s = sqrt(s2);
-    if (fabs(h) > 1e-3 * s) return (Fb - Fa) / (2.0 * h);
     const double r = 1.0 / s2, m2 = m * m, h2 = h * h;
     // f'' = s2^{-3/2}, f'''' = (12 m^2 - 3) s2^{-7/2}, f^(6) = (45 - 540 m^2 + 360 m^4) s2^{-11/2}
     const double f2 = r / s;
@@ -62,12 +67,22 @@ template <> struct Arith<double> {
     const double f6 = (45.0 - 540.0 * m2 + 360.0 * m2 * m2) * r * r * r * r * r / s;
     return s + h2 * (f2 / 24.0 + h2 * (f4 / 1920.0 + h2 * f6 / 322560.0));
   }
-  // nonlinear weights (Eq. WLOC1): returns omega_0, omega_2 from q_k = (eps + beta_k)^2
+  // nonlinear weights (Eq. WLOC1): returns omega_0, omega_2 from q_k = (eps + beta_k)^2 in the
+  // product form omega_k = d_k prod_{l != k} q_l / sum_m d_m prod_{l != m} q_l (one division;
+  // the quotients d_k / q_k of Eq. WLOC1 when the products leave the double range)
   __device__ __forceinline__ static void weights(double q0, double q1, double q2, double &w0, double &w2) {
-    const double a0 = 0.1 / q0, a1 = 0.6 / q1, a2 = 0.3 / q2;
-    const double sum = a0 + a1 + a2;
-    w0 = a0 / sum;
-    w2 = a2 / sum;
+    const double n0 = 0.1 * (q1 * q2), n2 = 0.3 * (q0 * q1);
+    const double den = fma(0.6, q0 * q2, n0 + n2);
+    if (den > 1e-290 && den < 1e290) {
+      const double r = 1.0 / den;
+      w0 = n0 * r;
+      w2 = n2 * r;
+    } else {
+      const double a0 = 0.1 / q0, a1 = 0.6 / q1, a2 = 0.3 / q2;
+      const double sum = a0 + a1 + a2;
+      w0 = a0 / sum;
+      w2 = a2 / sum;
+    }
   }
   __device__ __forceinline__ static double cosv(double x) { return cos(x); }
   __device__ __forceinline__ static double sinv(double x) { return sin(x); }
