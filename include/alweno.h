@@ -220,19 +220,16 @@ typedef struct alw_batch alw_batch;
 
 /* Work-list orders the autotuner chooses from. */
 enum { ALW_ORDER_INSTANCE = 0, ALW_ORDER_LARGEST_FIRST = 1, ALW_ORDER_INTERLEAVED = 2 };
-/* How the ordered work list maps onto the persistent CTAs (CTA c of G takes
- * entries c, c+G, c+2G, ...): STRIDED uses the ordered list as it is, so
- * consecutive entries run side by side on neighbouring CTAs; CTA_RUNS reorders
- * it so that each CTA takes one contiguous stretch of the ordered list (few
- * instance boundaries per CTA when instances are small).  The autotuner keeps
- * STRIDED, which measures faster in full stages; CTA_RUNS is a fixed choice. */
-enum { ALW_LAYOUT_STRIDED = 0, ALW_LAYOUT_CTA_RUNS = 1 };
-
 typedef struct {
   int32_t order;            /* ALW_ORDER_* */
   int32_t steps_per_graph;  /* RK3 steps captured per graph replay (1..256) */
   int32_t grid_ctas;        /* persistent CTAs; 0 = as many as fit on the device (larger values are capped) */
-  int32_t layout;           /* ALW_LAYOUT_* */
+  int32_t run;              /* entries of the ordered work list a persistent CTA takes in a row before
+                               the next CTA's turn (0..64): 1 = consecutive entries side by side on
+                               neighbouring CTAs; k > 1 = blocks of k, so a CTA changes instance (and
+                               folds that instance's alpha) less often while neighbouring blocks
+                               still run together; 0 = one contiguous stretch per CTA.  The
+                               autotuner uses 4. */
 } alw_batch_tuning;
 
 alw_status alw_batch_create(const alw_scheme *scheme, void *cuda_stream, alw_batch **out);

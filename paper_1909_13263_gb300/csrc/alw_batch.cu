@@ -119,6 +119,8 @@ struct alw_batch {
 
 namespace {
 
+constexpr int kDefaultRun = 4;  // work-list entries a CTA takes in a row (alw_batch_tuning::run)
+
 int cap_for(const alw_batch *b) {
   return b->prec == P_MIXED ? stage2d_grid_cap_mixed(b->scheme.weights) : stage2d_grid_cap_f32(b->scheme.weights);
 }
@@ -202,9 +204,9 @@ std::vector<int> ordered_list(const alw_batch *b, const std::vector<char> &live,
   return list;
 }
 
-// The work list of the live instances in the given order and layout (ALW_LAYOUT_*), for the CTA
-// count the launches will use.
-std::vector<int> work_list(alw_batch *b, const std::vector<char> &live, int order, int layout) {
+// The work list of the live instances in the given order, laid out over the CTAs the launches
+// will use in runs of `run` entries (alw_batch_tuning::run).
+std::vector<int> work_list(alw_batch *b, const std::vector<char> &live, int order, int run) {
   int kind = -1;
   bool uniform = true;
   for (size_t i = 0; i < b->h_inst.size(); ++i) {
@@ -214,9 +216,11 @@ std::vector<int> work_list(alw_batch *b, const std::vector<char> &live, int orde
   }
   b->kind1 = (uniform && kind >= 0) ? kind + 1 : 0;  // launches of this list use that kernel
   std::vector<int> list = ordered_list(b, live, order);
-  if (layout != ALW_LAYOUT_CTA_RUNS) return list;
+  if (run == 1) return list;
   std::vector<int> out;
-  cta_runs(list, stage2d_grid((int)list.size(), b->tuning.grid_ctas, b->grid_cap), out);
+  const int G = stage2d_grid((int)list.size(), b->tuning.grid_ctas, b->grid_cap);
+  if (run == 0) cta_runs(list, G, out);
+  else cta_blocks(list, G, run, out);
   return out;
 }
 
@@ -400,7 +404,7 @@ alw_status build(alw_batch *b) {
   for (auto &pd : b->pend) std::vector<double>().swap(pd.phi0);
   std::vector<char> live(n, 1);
   b->grid_cap = cap_for(b);
-  st = upload_list(b, work_list(b, live, ALW_ORDER_INSTANCE, ALW_LAYOUT_STRIDED));
+  st = upload_list(b, work_list(b, live, ALW_ORDER_INSTANCE, kDefaultRun));
   if (st) return st;
   st = prime_alpha(b, (int)total_tiles);
   if (st) return st;
@@ -456,13 +460,14 @@ alw_status autotune(alw_batch *b) {
   alw_batch_tuning best{};
   double best_ms = 1e30;
   const int orders[3] = {ALW_ORDER_INSTANCE, ALW_ORDER_LARGEST_FIRST, ALW_ORDER_INTERLEAVED};
-  // layouts: CTA runs time faster in these reduction-only trials (they make the per-run
-  // epilogue rare) but slower in full stages (neighbouring tiles no longer run side by side),
-  // so the autotuner keeps the strided layout; CTA runs stay available as a fixed tuning
-  const int layouts[1] = {ALW_LAYOUT_STRIDED};
+  // runs of 4 entries per CTA: each CTA changes instance (and closes a run) a quarter as often
+  // as with single entries while neighbouring blocks of tiles still run side by side (one
+  // contiguous stretch per CTA times fast in these reduction-only trials but loses in full
+  // stages, so the run length is fixed rather than tuned)
+  const int runs[1] = {kDefaultRun};
   b->tuning.grid_ctas = 0;
   for (int o : orders)
-    for (int l : layouts) {
+    for (int l : runs) {
       alw_status st = upload_list(b, work_list(b, live, o, l));
       if (st) return st;
       double ms;
@@ -473,7 +478,7 @@ alw_status autotune(alw_batch *b) {
       if (ms < best_ms) {
         best_ms = ms;
         best.order = o;
-        best.layout = l;
+        best.run = l;
       }
     }
   best.steps_per_graph = total >= 4096 ? 2 : (total >= 512 ? 8 : 32);
@@ -555,7 +560,7 @@ alw_status alw_batch_set_tuning(alw_batch *b, const alw_batch_tuning *t) {
   }
   if (t->order < ALW_ORDER_INSTANCE || t->order > ALW_ORDER_INTERLEAVED || t->steps_per_graph < 1 ||
       t->steps_per_graph > 256 || t->grid_ctas < 0 ||
-      (t->layout != ALW_LAYOUT_STRIDED && t->layout != ALW_LAYOUT_CTA_RUNS))
+      t->run < 0 || t->run > 64)
     return berr(ALW_EINVAL, "bad tuning");
   b->tuning = *t;
   b->user_tuning = true;
@@ -604,7 +609,7 @@ alw_status alw_batch_run(alw_batch *b, int64_t *replays_out) {
   int stalls = 0;
   long long last_steps_sum = -1;
   while (nlive > 0) {
-    std::vector<int> list = work_list(b, live, b->tuning.order, b->tuning.layout);
+    std::vector<int> list = work_list(b, live, b->tuning.order, b->tuning.run);
     st = upload_list(b, list);
     if (st) return st;
     st = build_graph(b, b->tuning.steps_per_graph, (int)list.size());

@@ -52,6 +52,35 @@ inline int stage2d_grid(int ntiles, int grid_ctas, int cap) {
 // instance-major list so that each CTA's entries form one contiguous stretch of it: a CTA then
 // meets few instance boundaries (each closes a run: alpha fold, counter atomics, a fence) and
 // walks neighbouring tiles of one instance in turn.
+// Block-cyclic layout: CTA c takes blocks of R consecutive entries of the ordered list, the
+// blocks dealt round-robin over the G CTAs (R = 1 is the list as it is).
+inline void cta_blocks(const std::vector<int> &in, int G, int R, std::vector<int> &out) {
+  const int n = (int)in.size();
+  out.resize(n);
+  if (G <= 0 || n == 0) return;
+  // the kernel's k-th entry of CTA c sits at position c + k G; give it list entry
+  // (k / R) G R + c R + k % R while that exists, and lay the leftovers out in order
+  std::vector<char> used(n, 0);
+  std::vector<int> pos(n, -1);
+  for (int p = 0; p < n; ++p) {
+    const int c = p % G, k = p / G;
+    const long long i = (long long)(k / R) * G * R + (long long)c * R + k % R;
+    if (i < n) {
+      pos[p] = (int)i;
+      used[i] = 1;
+    }
+  }
+  int next = 0;
+  for (int p = 0; p < n; ++p) {
+    if (pos[p] < 0) {
+      while (used[next]) ++next;
+      pos[p] = next;
+      used[next] = 1;
+    }
+    out[p] = in[pos[p]];
+  }
+}
+
 inline void cta_runs(const std::vector<int> &in, int G, std::vector<int> &out) {
   const int n = (int)in.size();
   out.resize(n);

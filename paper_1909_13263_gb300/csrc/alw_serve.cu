@@ -376,7 +376,7 @@ void copier_main(alw_server *s) {
 // Compute thread: rounds of RK steps over every active instance.
 void worker_main(alw_server *s) {
   cudaSetDevice(s->device);
-  std::vector<int> list, new_tiles;
+  std::vector<int> list, new_tiles, tmp;
   std::vector<Request *> active, round;  // active: in admission order
   for (;;) {
     std::vector<Request *> fresh;
@@ -424,6 +424,11 @@ void worker_main(alw_server *s) {
       }
       r->primed = true;
     }
+    // each CTA takes its entries in blocks of 4 (fewer instance changes per CTA)
+    cta_blocks(list, stage2d_grid((int)list.size(), 0, s->grid_cap), 4, tmp);
+    list.swap(tmp);
+    cta_blocks(new_tiles, stage2d_grid((int)new_tiles.size(), 0, s->grid_cap), 4, tmp);
+    new_tiles.swap(tmp);
     // a round whose members share one Hamiltonian runs that Hamiltonian's own kernel
     int kind1 = round.empty() ? 0 : round.front()->ham + 1;
     for (Request *r : round)

@@ -65,11 +65,10 @@ class State(ctypes.Structure):
 
 class BatchTuning(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int32), ("steps_per_graph", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
-                ("layout", ctypes.c_int32)]
+                ("run", ctypes.c_int32)]
 
 
 ORDER = {"instance": 0, "largest_first": 1, "interleaved": 2}
-LAYOUT = {"strided": 0, "cta_runs": 1}
 
 
 class RequestInfo(ctypes.Structure):
@@ -352,20 +351,19 @@ class Batch:
         self.shapes.append((ny, nx))
         return i.value
 
-    def set_tuning(self, order: str = None, steps_per_graph: int = 4, grid_ctas: int = 0, layout: str = "strided"):
+    def set_tuning(self, order: str = None, steps_per_graph: int = 4, grid_ctas: int = 0, run: int = 4):
         if order is None:
             check(self._L.alw_batch_set_tuning(self._h, None))
             return
-        t = BatchTuning(ORDER[order], steps_per_graph, grid_ctas, LAYOUT[layout])
+        t = BatchTuning(ORDER[order], steps_per_graph, grid_ctas, run)
         check(self._L.alw_batch_set_tuning(self._h, ctypes.byref(t)))
 
     def tuning(self) -> dict:
         t = BatchTuning()
         check(self._L.alw_batch_get_tuning(self._h, ctypes.byref(t)))
         inv = {v: k for k, v in ORDER.items()}
-        linv = {v: k for k, v in LAYOUT.items()}
         return {"order": inv.get(t.order, t.order), "steps_per_graph": t.steps_per_graph, "grid_ctas": t.grid_ctas,
-                "layout": linv.get(t.layout, t.layout)}
+                "run": t.run}
 
     def build(self):
         """Upload the instances and tune the work list now (run() does it on first use)."""

@@ -54,10 +54,10 @@ def test_batch_equals_single_solves(precision, weights, uniform):
             assert np.array_equal(got, ref), (k, inst, float(np.max(np.abs(got - ref))))
 
 
-@pytest.mark.parametrize("layout", ["strided", "cta_runs"])
-def test_batch_fixed_tuning_orders_agree(layout):
-    # every order, both layouts of the work list over the CTAs, and a CTA count below the
-    # occupancy cap (so that many CTAs hold runs over several instances) give identical results
+@pytest.mark.parametrize("run", [1, 4, 0])
+def test_batch_fixed_tuning_orders_agree(run):
+    # every order, runs of 1 and 4 entries per CTA and one stretch per CTA, and a CTA count below
+    # the occupancy cap (so that many CTAs hold runs over several instances) give identical results
     insts = _mix(6, 32, 160, seed=5)
     outs = []
     for order, ctas in (("instance", 0), ("largest_first", 0), ("interleaved", 0), ("instance", 7)):
@@ -66,10 +66,10 @@ def test_batch_fixed_tuning_orders_agree(layout):
                 phi0, _ = inputs.instance_phi0(inst)
                 b.add(nx=inst.n, ny=inst.n, xlo=-2.0, xhi=2.0, ylo=-2.0, yhi=2.0, ham=inst.ham, phi0=phi0,
                       t_final=inst.t_final)
-            b.set_tuning(order=order, steps_per_graph=3, grid_ctas=ctas, layout=layout)
+            b.set_tuning(order=order, steps_per_graph=3, grid_ctas=ctas, run=run)
             b.run()
             tun = b.tuning()
-            assert tun["order"] == order and tun["layout"] == layout and tun["grid_ctas"] == ctas
+            assert tun["order"] == order and tun["run"] == run and tun["grid_ctas"] == ctas
             outs.append([b.get_phi(k) for k in range(len(insts))])
     for o in outs[1:]:
         for a, c in zip(outs[0], o):
