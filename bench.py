@@ -452,10 +452,11 @@ def run_ours(args):
 def run_precision_report(args):
     """Errors of the float paths against FP64 and against the exact solution (one JSON line).
 
-    Example 3 (periodic, exact solution by characteristics) on 400^2 and 2048^2 to t = 0.5/pi^2:
-    L1 (mean |e|) and max |e| of FP64, MIXED and FP32 against the exact solution, and of MIXED and
-    FP32 against FP64.  Example 10 (sin(p+q), pi(|y|-|x|), linear extrapolation) on 1024^2 to t = 1:
-    MIXED and FP32 against FP64 (no exact solution).  Plus FP64 throughput at 2048^2."""
+    Example 3 (periodic, exact solution by characteristics) to t = 0.5/pi^2 (default 400^2 and
+    2048^2): L1 (mean |e|) and max |e| of FP64, MIXED and FP32 against the exact solution, and of
+    MIXED and FP32 against FP64.  Example 10 (sin(p+q), pi(|y|-|x|), linear extrapolation) to t = 1
+    (default 1024^2): MIXED and FP32 against FP64 (no exact solution).  Plus FP64 throughput at
+    2048^2."""
     import numpy as np
     import torch
 
@@ -467,7 +468,7 @@ def run_precision_report(args):
     native.use_torch_allocator(True)
     out = {"report": "precision"}
     tf = 0.5 / math.pi**2
-    for n in (400, 2048):
+    for n in [int(v) for v in args.report_ex3_sizes.split(",") if v]:
         x, dx = inputs.axis(n, -2.0, 2.0, "periodic")
         phi0 = inputs.phi0_negcos_diag_2d(x, x)
         ex = exact.negcos_diag_2d("burgers2d", x, x, tf)
@@ -487,21 +488,22 @@ def run_precision_report(args):
                 row[prec].update({"l1_vs_fp64": float(d.mean()), "linf_vs_fp64": float(d.max()),
                                   "l1_ratio_to_fp64": float(e.mean() / np.abs(res["fp64"] - ex).mean())})
         out[f"ex3_burgers2d_{n}sq"] = row
-    n = 1024
-    x, dx = inputs.axis(n, -1.0, 1.0, "linextrap")
-    phi0 = inputs.phi0_riemann_2d(x, x)
-    res = {}
-    for prec in ("fp64", "mixed", "fp32"):
-        with native.Solver(dim=2, nx=n, ny=n, bc="linextrap", xlo=-1.0, xhi=1.0, ylo=-1.0, yhi=1.0, ham="sin2d",
-                           precision=prec) as s:
-            s.set_phi0(phi0)
-            steps = s.step_to(1.0)
-            res[prec] = s.get_phi()
-    row = {"steps": steps}
-    for prec in ("mixed", "fp32"):
-        d = np.abs(res[prec] - res["fp64"])
-        row[prec] = {"l1_vs_fp64": float(d.mean()), "linf_vs_fp64": float(d.max())}
-    out[f"ex10_sin2d_linextrap_{n}sq"] = row
+    for n in [int(v) for v in args.report_ex10_sizes.split(",") if v]:
+        x, dx = inputs.axis(n, -1.0, 1.0, "linextrap")
+        phi0 = inputs.phi0_riemann_2d(x, x)
+        res = {}
+        for prec in ("fp64", "mixed", "fp32"):
+            with native.Solver(dim=2, nx=n, ny=n, bc="linextrap", xlo=-1.0, xhi=1.0, ylo=-1.0, yhi=1.0,
+                               ham="sin2d", precision=prec) as s:
+                s.set_phi0(phi0)
+                steps = s.step_to(1.0)
+                res[prec] = s.get_phi()
+        row = {"steps": steps}
+        for prec in ("mixed", "fp32"):
+            d = np.abs(res[prec] - res["fp64"])
+            row[prec] = {"l1_vs_fp64": float(d.mean()), "linf_vs_fp64": float(d.max())}
+        out[f"ex10_sin2d_linextrap_{n}sq"] = row
+        del res
     # FP64 throughput (the parity path): RK3 steps of Example 3 on 2048^2
     n = 2048
     x, dx = inputs.axis(n, -2.0, 2.0, "periodic")
@@ -548,6 +550,10 @@ def main():
     ap.add_argument("--serve-rates", type=str, default="", help="comma-separated arrival rates (a sweep)")
     ap.add_argument("--report", choices=["", "precision"], default="",
                     help="precision: errors of the float paths against FP64 and the exact solution")
+    ap.add_argument("--report-ex3-sizes", type=str, default="400,2048",
+                    help="precision report: grid sides of Example 3 (comma-separated)")
+    ap.add_argument("--report-ex10-sizes", type=str, default="1024",
+                    help="precision report: grid sides of Example 10 (comma-separated)")
     ap.add_argument("--serve-count", type=int, default=120)
     ap.add_argument("--serve-budget-gb", type=float, default=60.0)
     args = ap.parse_args()
