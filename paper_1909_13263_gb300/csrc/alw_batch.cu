@@ -108,7 +108,11 @@ struct alw_batch {
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0, graph_ntiles = 0;
   int grid_cap = 0;
-  int kind1 = 0;  // 1 + the Hamiltonian every instance of the current work list shares (0: mixed)
+  // the uploaded work list: one group of entries per Hamiltonian, back to back in d_tiles
+  struct Group {
+    int off, n, kind;
+  };
+  std::vector<Group> groups;
 
   void *alloc(size_t bytes) {
     void *p = dev_alloc(bytes, stream);
@@ -170,7 +174,6 @@ Stage2DParams batch_params(const alw_batch *b, int stage, int loop_mode, int nti
   }
   q.ntiles = ntiles;
   q.grid_ctas = b->tuning.grid_ctas;
-  q.batch_kind1 = b->kind1;
   q.insts = b->d_inst;
   q.states = b->d_state;
   q.tiles = b->d_tiles;
@@ -206,15 +209,7 @@ std::vector<int> ordered_list(const alw_batch *b, const std::vector<char> &live,
 
 // The work list of the live instances in the given order, laid out over the CTAs the launches
 // will use in runs of `run` entries (alw_batch_tuning::run).
-std::vector<int> work_list(alw_batch *b, const std::vector<char> &live, int order, int run) {
-  int kind = -1;
-  bool uniform = true;
-  for (size_t i = 0; i < b->h_inst.size(); ++i) {
-    if (!live[i]) continue;
-    if (kind < 0) kind = b->h_inst[i].ham;
-    uniform = uniform && b->h_inst[i].ham == kind;
-  }
-  b->kind1 = (uniform && kind >= 0) ? kind + 1 : 0;  // launches of this list use that kernel
+std::vector<int> work_list(const alw_batch *b, const std::vector<char> &live, int order, int run) {
   std::vector<int> list = ordered_list(b, live, order);
   if (run == 1) return list;
   std::vector<int> out;
@@ -224,20 +219,48 @@ std::vector<int> work_list(alw_batch *b, const std::vector<char> &live, int orde
   return out;
 }
 
-alw_status upload_list(alw_batch *b, const std::vector<int> &list) {
-  if ((int)list.size() > b->ntiles_alloc) return berr(ALW_EINVAL, "work list larger than allocated");
-  if (!list.empty())
-    B_CUDA(cudaMemcpyAsync(b->d_tiles, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+// Uploads the work list of the live instances as one group per Hamiltonian (each in the given
+// order and run layout), so that every launch runs the kernel specialised for its Hamiltonian.
+// Returns the number of entries.
+alw_status upload_groups(alw_batch *b, const std::vector<char> &live, int order, int run, int *total) {
+  std::vector<int> all;
+  b->groups.clear();
+  for (int kind = 0; kind < 16; ++kind) {
+    std::vector<char> sel(live.size(), 0);
+    bool any = false;
+    for (size_t i = 0; i < live.size(); ++i)
+      if (live[i] && b->h_inst[i].ham == kind) sel[i] = 1, any = true;
+    if (!any) continue;
+    const std::vector<int> list = work_list(b, sel, order, run);
+    b->groups.push_back({(int)all.size(), (int)list.size(), kind});
+    all.insert(all.end(), list.begin(), list.end());
+  }
+  if ((int)all.size() > b->ntiles_alloc) return berr(ALW_EINVAL, "work list larger than allocated");
+  if (!all.empty())
+    B_CUDA(cudaMemcpyAsync(b->d_tiles, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
   B_CUDA(cudaStreamSynchronize(b->stream));
+  if (total) *total = (int)all.size();
   return ALW_OK;
 }
 
-alw_status enqueue_steps(alw_batch *b, int loop_mode, int nsteps, int ntiles, double dt_stage) {
+// One stage (0: reduction only) over every group of the uploaded work list.
+alw_status launch_groups(alw_batch *b, int stage, int loop_mode, double dt_stage, int write_slot = -2) {
+  for (const auto &g : b->groups) {
+    Stage2DParams q = batch_params(b, stage, loop_mode, g.n);
+    q.tiles = b->d_tiles + g.off;
+    q.batch_kind1 = g.kind + 1;
+    q.p.dt_value = dt_stage;
+    if (write_slot != -2) q.p.write_slot = write_slot;
+    B_LAUNCH(launch(b, q));
+  }
+  return ALW_OK;
+}
+
+alw_status enqueue_steps(alw_batch *b, int loop_mode, int nsteps, double dt_stage) {
   for (int s = 0; s < nsteps; ++s)
     for (int stage = 1; stage <= 3; ++stage) {
-      Stage2DParams q = batch_params(b, stage, loop_mode, ntiles);
-      q.p.dt_value = dt_stage;
-      B_LAUNCH(launch(b, q));
+      alw_status st = launch_groups(b, stage, loop_mode, dt_stage);
+      if (st) return st;
     }
   return ALW_OK;
 }
@@ -249,7 +272,7 @@ alw_status build_graph(alw_batch *b, int nsteps, int ntiles) {
   }
   cudaGraph_t g = nullptr;
   B_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-  alw_status st = enqueue_steps(b, LOOP_STEP_TO, nsteps, ntiles, 0.0);
+  alw_status st = enqueue_steps(b, LOOP_STEP_TO, nsteps, 0.0);
   cudaError_t e = cudaStreamEndCapture(b->stream, &g);
   if (st != ALW_OK) {
     if (g) cudaGraphDestroy(g);
@@ -264,10 +287,7 @@ alw_status build_graph(alw_batch *b, int nsteps, int ntiles) {
   return ALW_OK;
 }
 
-alw_status prime_alpha(alw_batch *b, int ntiles) {
-  B_LAUNCH(launch(b, batch_params(b, 0, LOOP_ADVANCE, ntiles)));
-  return ALW_OK;
-}
+alw_status prime_alpha(alw_batch *b) { return launch_groups(b, 0, LOOP_ADVANCE, 0.0); }
 
 // Lay out the arena, upload every instance and prepare the device tables.
 alw_status build(alw_batch *b) {
@@ -404,9 +424,9 @@ alw_status build(alw_batch *b) {
   for (auto &pd : b->pend) std::vector<double>().swap(pd.phi0);
   std::vector<char> live(n, 1);
   b->grid_cap = cap_for(b);
-  st = upload_list(b, work_list(b, live, ALW_ORDER_INSTANCE, kDefaultRun));
+  st = upload_groups(b, live, ALW_ORDER_INSTANCE, kDefaultRun, nullptr);
   if (st) return st;
-  st = prime_alpha(b, (int)total_tiles);
+  st = prime_alpha(b);
   if (st) return st;
   B_CUDA(cudaStreamSynchronize(b->stream));
   b->built = true;
@@ -414,18 +434,13 @@ alw_status build(alw_batch *b) {
 }
 
 // Time `passes` reduction-only sweeps over the work list (no stores; alpha goes to the unused slot 3).
-alw_status trial(alw_batch *b, int ntiles, int passes, double *ms) {
+alw_status trial(alw_batch *b, int passes, double *ms) {
   cudaEvent_t e0, e1;
   B_CUDA(cudaEventCreate(&e0));
   B_CUDA(cudaEventCreate(&e1));
   B_CUDA(cudaEventRecord(e0, b->stream));
   alw_status st = ALW_OK;
-  for (int i = 0; i < passes && st == ALW_OK; ++i) {
-    Stage2DParams q = batch_params(b, 0, LOOP_ADVANCE, ntiles);
-    q.p.write_slot = 3;
-    const int le = launch(b, q);
-    if (le) st = berr(ALW_ECUDA, "trial launch: %s", cudaGetErrorString((cudaError_t)le));
-  }
+  for (int i = 0; i < passes && st == ALW_OK; ++i) st = launch_groups(b, 0, LOOP_ADVANCE, 0.0, 3);
   B_CUDA(cudaEventRecord(e1, b->stream));
   B_CUDA(cudaEventSynchronize(e1));
   float f = 0;
@@ -468,12 +483,12 @@ alw_status autotune(alw_batch *b) {
   b->tuning.grid_ctas = 0;
   for (int o : orders)
     for (int l : runs) {
-      alw_status st = upload_list(b, work_list(b, live, o, l));
+      alw_status st = upload_groups(b, live, o, l, nullptr);
       if (st) return st;
       double ms;
-      st = trial(b, (int)total, 1, &ms);  // warm-up
+      st = trial(b, 1, &ms);  // warm-up
       if (st) return st;
-      st = trial(b, (int)total, 3, &ms);
+      st = trial(b, 3, &ms);
       if (st) return st;
       if (ms < best_ms) {
         best_ms = ms;
@@ -609,12 +624,11 @@ alw_status alw_batch_run(alw_batch *b, int64_t *replays_out) {
   int stalls = 0;
   long long last_steps_sum = -1;
   while (nlive > 0) {
-    std::vector<int> list = work_list(b, live, b->tuning.order, b->tuning.run);
-    st = upload_list(b, list);
+    int ntiles_now = 0;
+    st = upload_groups(b, live, b->tuning.order, b->tuning.run, &ntiles_now);
     if (st) return st;
-    st = build_graph(b, b->tuning.steps_per_graph, (int)list.size());
+    st = build_graph(b, b->tuning.steps_per_graph, ntiles_now);
     if (st) return st;
-    const int ntiles_now = (int)list.size();
     // replay until half of this work list is dead, then compact it
     for (;;) {
       B_CUDA(cudaGraphLaunch(b->graph, b->stream));

@@ -122,7 +122,6 @@ struct alw_server {
   int max_slots = 0, max_side = 0, steps_per_round = 2;
   int round_tiles = 0;  // tile limit of a round beyond its oldest instance (0: none)
   int grid_cap = 1;     // CTAs of the persistent stage kernel that fit on the device
-  int kind1 = 0;        // 1 + the Hamiltonian all members of the current round share (0: mixed)
   int pitch = 0;
   long long rows_total = 0;
   void *arr[6] = {};
@@ -200,7 +199,6 @@ Stage2DParams server_params(const alw_server *s, int stage, int loop_mode, int n
     q.map_c = -1;
   }
   q.ntiles = ntiles;
-  q.batch_kind1 = s->kind1;
   q.states = s->d_state;
   q.insts = s->d_inst;
   q.tiles = s->d_tiles;
@@ -415,42 +413,48 @@ void worker_main(alw_server *s) {
       }
       if (rem_min < 1e29) steps = std::max(steps, std::min(16, (int)rem_min));
     }
+    // work lists of the round, one group per Hamiltonian (each launch runs that Hamiltonian's own
+    // kernel), each in admission order and laid out over the CTAs in blocks of 4 entries (fewer
+    // instance changes per CTA): first the new instances' first-alpha pass, then the steps
+    struct Seg {
+      int off, n, kind;
+    };
+    std::vector<Seg> prime_segs, step_segs;
     list.clear();
-    new_tiles.clear();
-    for (Request *r : round) {
-      for (int t = 0; t < s->h_inst[r->slot].ntiles; ++t) {
-        list.push_back(r->slot * 65536 + t);
-        if (!r->primed) new_tiles.push_back(r->slot * 65536 + t);
+    auto add_groups = [&](bool only_new, std::vector<Seg> &segs) {
+      for (int kind = 0; kind < 16; ++kind) {
+        new_tiles.clear();
+        for (Request *r : round)
+          if (r->ham == kind && (!only_new || !r->primed))
+            for (int t = 0; t < s->h_inst[r->slot].ntiles; ++t) new_tiles.push_back(r->slot * 65536 + t);
+        if (new_tiles.empty()) continue;
+        cta_blocks(new_tiles, stage2d_grid((int)new_tiles.size(), 0, s->grid_cap), 4, tmp);
+        segs.push_back({(int)list.size(), (int)tmp.size(), kind});
+        list.insert(list.end(), tmp.begin(), tmp.end());
       }
-      r->primed = true;
-    }
-    // each CTA takes its entries in blocks of 4 (fewer instance changes per CTA)
-    cta_blocks(list, stage2d_grid((int)list.size(), 0, s->grid_cap), 4, tmp);
-    list.swap(tmp);
-    cta_blocks(new_tiles, stage2d_grid((int)new_tiles.size(), 0, s->grid_cap), 4, tmp);
-    new_tiles.swap(tmp);
-    // a round whose members share one Hamiltonian runs that Hamiltonian's own kernel
-    int kind1 = round.empty() ? 0 : round.front()->ham + 1;
-    for (Request *r : round)
-      if (r->ham + 1 != kind1) kind1 = 0;
-    s->kind1 = kind1;
-    cudaError_t e = cudaSuccess;
+    };
+    add_groups(true, prime_segs);
+    add_groups(false, step_segs);
+    for (Request *r : round) r->primed = true;
+    cudaError_t e = cudaMemcpyAsync(s->d_tiles, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                    s->stream);
     int le = 0;
-    if (!new_tiles.empty()) {  // first lagged alpha of the new instances
-      e = cudaMemcpyAsync(s->d_tiles, new_tiles.data(), new_tiles.size() * sizeof(int), cudaMemcpyHostToDevice,
-                          s->stream);
-      if (e == cudaSuccess) le = launch(s, server_params(s, 0, LOOP_ADVANCE, (int)new_tiles.size()));
+    for (const Seg &g : prime_segs) {  // first lagged alpha of the new instances
+      if (e != cudaSuccess || le) break;
+      Stage2DParams q = server_params(s, 0, LOOP_ADVANCE, g.n);
+      q.tiles = s->d_tiles + g.off;
+      q.batch_kind1 = g.kind + 1;
+      le = launch(s, q);
     }
-    if (e == cudaSuccess && !le)
-      e = cudaMemcpyAsync(s->d_tiles + new_tiles.size(), list.data(), list.size() * sizeof(int),
-                          cudaMemcpyHostToDevice, s->stream);
-    Stage2DParams q;
     for (int k = 0; k < steps && e == cudaSuccess && !le; ++k)
-      for (int stage = 1; stage <= 3 && !le; ++stage) {
-        q = server_params(s, stage, LOOP_STEP_TO, (int)list.size());
-        q.tiles = s->d_tiles + new_tiles.size();
-        le = launch(s, q);
-      }
+      for (int stage = 1; stage <= 3 && !le; ++stage)
+        for (const Seg &g : step_segs) {
+          if (le) break;
+          Stage2DParams q = server_params(s, stage, LOOP_STEP_TO, g.n);
+          q.tiles = s->d_tiles + g.off;
+          q.batch_kind1 = g.kind + 1;
+          le = launch(s, q);
+        }
     if (e == cudaSuccess && !le)
       e = cudaMemcpyAsync(s->h_state, s->d_state, sizeof(DevState) * s->max_slots, cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess && !le) e = cudaStreamSynchronize(s->stream);
