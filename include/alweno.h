@@ -233,8 +233,9 @@ typedef struct {
 } alw_batch_tuning;
 
 alw_status alw_batch_create(const alw_scheme *scheme, void *cuda_stream, alw_batch **out);
-/* Add an instance (grid dim 2, periodic; host_phi0 of n = nx*ny doubles, copied).
- * id_out receives its index.  ALW_EBUSY after the batch has run. */
+/* Add an instance (grid dim 2, periodic; host_phi0 of n = nx*ny doubles, copied to
+ * device memory before the call returns, so the caller may reuse it).  id_out
+ * receives its index.  ALW_EBUSY after the batch has been built or run. */
 alw_status alw_batch_add(alw_batch *b, const alw_grid *grid, const alw_hamiltonian *ham, const double *host_phi0,
                          size_t n, double t_final, int32_t *id_out);
 /* Fix the tuning (NULL: let the autotuner choose on the next run). */

@@ -83,7 +83,8 @@ struct alw_batch {
     alw_grid grid;
     int ham;
     double t_final;
-    std::vector<double> phi0;
+    double *dev_phi0;  // phi0 copied to the device when the instance is added (freed by build)
+    size_t n;
   };
   std::vector<Pending> pend;
   // device side (built on the first run)
@@ -124,6 +125,15 @@ struct alw_batch {
 namespace {
 
 constexpr int kDefaultRun = 4;  // work-list entries a CTA takes in a row (alw_batch_tuning::run)
+
+// Releases the device copies of phi0 held for instances not yet built into the arena.
+void free_pending(alw_batch *b) {
+  for (auto &pd : b->pend)
+    if (pd.dev_phi0) {
+      dev_free(pd.dev_phi0, pd.n * sizeof(double), b->stream);
+      pd.dev_phi0 = nullptr;
+    }
+}
 
 int cap_for(const alw_batch *b) {
   return b->prec == P_MIXED ? stage2d_grid_cap_mixed(b->scheme.weights) : stage2d_grid_cap_f32(b->scheme.weights);
@@ -371,26 +381,13 @@ alw_status build(alw_batch *b) {
     const int r = encode_tile_map(&b->maps[i], bases[i], pitch, rows);
     if (r) return berr(ALW_ECUDA, "cuTensorMapEncodeTiled failed (%d)", r);
   }
-  // upload phi0 of every instance into its block of rows: all instances are staged in one device
-  // buffer (copies queued back to back), then split into the arena with its ghost frame, with
-  // a single synchronisation at the end
-  size_t total_n = 0;
-  for (auto &pd : b->pend) total_n += pd.phi0.size();
-  double *stage = (double *)dev_alloc(total_n * sizeof(double), b->stream);
-  if (!stage) return berr(ALW_ENOMEM, "device allocation of %zu bytes failed", total_n * sizeof(double));
+  // split phi0 of every instance (on the device since it was added) into its block of rows with
+  // its ghost frame; one synchronisation at the end
   alw_status st = ALW_OK;
-  size_t off_n = 0;
   for (int i = 0; i < n && st == ALW_OK; ++i) {
     const InstDesc &d = b->h_inst[i];
     const size_t off = (size_t)d.row_off * pitch;  // element offset of the instance's first row
-    double *src = stage + off_n;
-    off_n += b->pend[i].phi0.size();
-    cudaError_t e = cudaMemcpyAsync(src, b->pend[i].phi0.data(), b->pend[i].phi0.size() * sizeof(double),
-                                    cudaMemcpyHostToDevice, b->stream);
-    if (e != cudaSuccess) {
-      st = berr(ALW_ECUDA, "upload: %s", cudaGetErrorString(e));
-      break;
-    }
+    const double *src = b->pend[i].dev_phi0;
     int le;
     if (b->prec == P_MIXED)
       le = launch_mixed_split(src, (float *)b->H[0] + off, (float *)b->Lo[0] + off, d.nx, d.ny, pitch, 2, b->stream);
@@ -418,10 +415,9 @@ alw_status build(alw_batch *b) {
     le = launch_ghosts(g, b->stream);
     if (le) st = berr(ALW_ECUDA, "ghost kernel: %s", cudaGetErrorString((cudaError_t)le));
   }
-  cudaStreamSynchronize(b->stream);  // the staging buffer is released only after its readers
-  dev_free(stage, total_n * sizeof(double), b->stream);
+  cudaStreamSynchronize(b->stream);  // the staged copies are released only after their readers
+  free_pending(b);
   if (st) return st;
-  for (auto &pd : b->pend) std::vector<double>().swap(pd.phi0);
   std::vector<char> live(n, 1);
   b->grid_cap = cap_for(b);
   st = upload_groups(b, live, ALW_ORDER_INSTANCE, kDefaultRun, nullptr);
@@ -560,8 +556,17 @@ alw_status alw_batch_add(alw_batch *b, const alw_grid *grid, const alw_hamiltoni
   p.grid = *grid;
   p.ham = ham->kind;
   p.t_final = t_final;
-  p.phi0.assign(host_phi0, host_phi0 + n);
-  b->pend.push_back(std::move(p));
+  p.n = n;
+  // copy phi0 to the device now (the caller may reuse its buffer on return)
+  p.dev_phi0 = (double *)dev_alloc(n * sizeof(double), b->stream);
+  if (!p.dev_phi0) return berr(ALW_ENOMEM, "device allocation of %zu bytes failed", n * sizeof(double));
+  cudaError_t e = cudaMemcpyAsync(p.dev_phi0, host_phi0, n * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    dev_free(p.dev_phi0, n * sizeof(double), b->stream);
+    return berr(ALW_ECUDA, "upload: %s", cudaGetErrorString(e));
+  }
+  b->pend.push_back(p);
   if (id_out) *id_out = (int32_t)(b->pend.size() - 1);
   return ALW_OK;
 }
@@ -713,6 +718,7 @@ alw_status alw_batch_memory_bytes(alw_batch *b, size_t *bytes) {
 alw_status alw_batch_destroy(alw_batch *b) {
   if (!b) return ALW_OK;
   cudaStreamSynchronize(b->stream);
+  free_pending(b);
   if (b->graph) cudaGraphExecDestroy(b->graph);
   for (auto &a : b->allocs) dev_free(a.first, a.second, b->stream);
   cudaStreamSynchronize(b->stream);
