@@ -37,17 +37,8 @@ static int launch2d_one(const Stage2DParams &prm, cudaStream_t stream) {
 
 template <int PREC, int W>
 static int launch2d_h(const Stage2DParams &prm, cudaStream_t s) {
-  if (prm.insts) {
-    // a batch whose instances share one Hamiltonian runs that Hamiltonian's own kernel
-    switch (prm.batch_kind1 - 1) {
-      case H_BURGERS2D: return launch2d_one<PREC, W, H_BURGERS2D>(prm, s);
-      case H_NEGCOS2D: return launch2d_one<PREC, W, H_NEGCOS2D>(prm, s);
-      case H_SIN2D: return launch2d_one<PREC, W, H_SIN2D>(prm, s);
-      case H_EIKONAL2D: return launch2d_one<PREC, W, H_EIKONAL2D>(prm, s);
-      default: return launch2d_one<PREC, W, -1>(prm, s);
-    }
-  }
-  switch (prm.inst0.ham) {
+  // a single instance's Hamiltonian, or the one every entry of a batch group shares
+  switch (prm.insts ? prm.batch_kind1 - 1 : prm.inst0.ham) {
     case H_BURGERS2D: return launch2d_one<PREC, W, H_BURGERS2D>(prm, s);
     case H_NEGCOS2D: return launch2d_one<PREC, W, H_NEGCOS2D>(prm, s);
     case H_SIN2D: return launch2d_one<PREC, W, H_SIN2D>(prm, s);
@@ -65,7 +56,7 @@ static int launch2d_impl(const Stage2DParams &prm, void *stream) {
 
 template <int PREC>
 static int grid_cap_impl(int weights) {
-  return weights == W_JP ? grid_cap_of<PREC, W_JP, -1>() : grid_cap_of<PREC, W_ARCLEN, -1>();
+  return weights == W_JP ? grid_cap_of<PREC, W_JP, H_BURGERS2D>() : grid_cap_of<PREC, W_ARCLEN, H_BURGERS2D>();
 }
 
 }  // namespace alw

@@ -30,7 +30,7 @@ struct Stage2DParams {
   int map_a, map_b, map_c;  // FP32: source, base (-1: none); MIXED: hi base index, lo base index, delta (-1: none)
   int ntiles;               // work-list length
   int grid_ctas;            // persistent CTAs to launch (0: as many as fit; never more than fit or ntiles)
-  int batch_kind1;          // batch: 1 + the Hamiltonian all listed instances share (0: they differ)
+  int batch_kind1;          // batch: 1 + the Hamiltonian every listed instance has
   const InstDesc *insts;    // batch: instance table (nullptr: the single instance `inst0`)
   DevState *states;         // batch: state of instance i at states + i (nullptr: read insts[i].st)
   const int *tiles;         // batch: work list, entry = instance * 65536 + tile of that instance

@@ -90,36 +90,14 @@ template <> struct Ham2<H_OPTCTRL2D> {
   }
 };
 
-// Compile-time kind H >= 0, or H = -1: the kind is read per instance (batches mixing Hamiltonians).
+// The Hamiltonian of a launch (compile-time kind; batches launch one group per Hamiltonian).
 template <int H> struct HamSel {
-  int kind;
   __device__ __forceinline__ float value(float p, float q, float x, float y) const {
     return Ham2<H>::value(p, q, x, y);
   }
   __device__ __forceinline__ void alpha(float um, float up, float vm, float vp, float x, float y, float &ax,
                                         float &ay) const {
     Ham2<H>::alpha(um, up, vm, vp, x, y, ax, ay);
-  }
-};
-// batches and the server hold position-free Hamiltonians only (checked on the host)
-template <> struct HamSel<-1> {
-  int kind;
-  __device__ __forceinline__ float value(float p, float q, float x, float y) const {
-    switch (kind) {
-      case H_NEGCOS2D: return Ham2<H_NEGCOS2D>::value(p, q, x, y);
-      case H_SIN2D: return Ham2<H_SIN2D>::value(p, q, x, y);
-      case H_EIKONAL2D: return Ham2<H_EIKONAL2D>::value(p, q, x, y);
-      default: return Ham2<H_BURGERS2D>::value(p, q, x, y);
-    }
-  }
-  __device__ __forceinline__ void alpha(float um, float up, float vm, float vp, float x, float y, float &ax,
-                                        float &ay) const {
-    switch (kind) {
-      case H_NEGCOS2D: Ham2<H_NEGCOS2D>::alpha(um, up, vm, vp, x, y, ax, ay); break;
-      case H_SIN2D: Ham2<H_SIN2D>::alpha(um, up, vm, vp, x, y, ax, ay); break;
-      case H_EIKONAL2D: Ham2<H_EIKONAL2D>::alpha(um, up, vm, vp, x, y, ax, ay); break;
-      default: Ham2<H_BURGERS2D>::alpha(um, up, vm, vp, x, y, ax, ay);
-    }
   }
 };
 
@@ -332,7 +310,7 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
     const TileInfo &d = s_info[buf];  // this tile's instance fields (shared memory)
     const int nx = d.nx, ny = d.ny, tx0 = d.tx0, ty0 = d.ty0;
     const size_t rbase = (size_t)d.row_off * p.pitch;   // element offset of the instance's rows
-    const HamSel<H> ham{d.ham};
+    const HamSel<H> ham;
     const float dtf = s_info[buf].dtf, fax = s_info[buf].fax, fay = s_info[buf].fay;
     const float *A = raw + buf * NARR * ARR;
     const float *B = A + ARR;
