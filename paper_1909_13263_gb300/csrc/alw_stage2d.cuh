@@ -22,6 +22,8 @@
 // last tile closes the instance's stage (dt, time, step count, buffer flip),
 // so instances advance independently.
 #pragma once
+#include <type_traits>
+
 #include "alw_device.cuh"
 #include "alw_params2d.h"
 #include "alw_sweep32.cuh"
@@ -317,28 +319,36 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
     const float *C = A + 2 * ARR;
     const bool has_delta = PREC == P_MIXED && prm.map_c >= 0;
 
-    // ---- 1. differences (rows by warp, columns by lane: no division, conflict-free)
-    auto cell_diff = [&](int i0, int i1) -> float {
-      if (PREC == P_MIXED) {
-        return (A[i1] - A[i0]) + ((B[i1] - B[i0]) + (has_delta ? (C[i1] - C[i0]) : 0.0f));
-      } else {
-        return A[i1] - A[i0];
+    // ---- 1. differences (rows by warp, columns by lane: no division, conflict-free); the
+    // MIXED variant without a delta array (stage 1) is a separate loop, so that it reads two
+    // arrays, not three
+    auto diff_pass = [&](auto with_delta) {
+      constexpr bool WD = decltype(with_delta)::value;
+      auto cell_diff = [&](int i0, int i1) -> float {
+        if (PREC == P_MIXED) {
+          if (WD) return (A[i1] - A[i0]) + ((B[i1] - B[i0]) + (C[i1] - C[i0]));
+          return (A[i1] - A[i0]) + (B[i1] - B[i0]);
+        } else {
+          return A[i1] - A[i0];
+        }
+      };
+      for (int r = warp; r < TY; r += NT / 32) {
+#pragma unroll
+        for (int c = lane; c < DXW; c += 32) {
+          const int i0 = (r + 3) * SW + c + 1;
+          dX[r * DXP + c] = cell_diff(i0, i0 + 1) * d.rdx;
+        }
+      }
+      for (int r = warp; r < DYH; r += NT / 32) {
+#pragma unroll
+        for (int c = lane; c < TX; c += 32) {
+          const int i0 = r * SW + c + 4;
+          dY[r * TX + c] = cell_diff(i0, i0 + SW) * d.rdy;
+        }
       }
     };
-    for (int r = warp; r < TY; r += NT / 32) {
-#pragma unroll
-      for (int c = lane; c < DXW; c += 32) {
-        const int i0 = (r + 3) * SW + c + 1;
-        dX[r * DXP + c] = cell_diff(i0, i0 + 1) * d.rdx;
-      }
-    }
-    for (int r = warp; r < DYH; r += NT / 32) {
-#pragma unroll
-      for (int c = lane; c < TX; c += 32) {
-        const int i0 = r * SW + c + 4;
-        dY[r * TX + c] = cell_diff(i0, i0 + SW) * d.rdy;
-      }
-    }
+    if (has_delta) diff_pass(std::true_type{});
+    else diff_pass(std::false_type{});
     __syncthreads();
 
     const bool edge = (tx0 < 3) || (tx0 + TX > nx - 3) || (ty0 < 3) || (ty0 + TY > ny - 3);
