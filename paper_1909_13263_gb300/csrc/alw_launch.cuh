@@ -20,11 +20,16 @@ static int launch_one(const StageParams &p, cudaStream_t stream) {
   return (int)cudaGetLastError();
 }
 
+// FP64 runs here in 1D and 2D; the float variants only in 1D (2D float stages run the persistent
+// TMA kernel, so their 2D instantiations of this kernel are not built).
 template <int PREC>
 static int launch_stage_impl(const StageParams &p, void *stream) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (p.dim == 2) {
-    return p.weights == W_JP ? launch_one<PREC, 2, W_JP>(p, s) : launch_one<PREC, 2, W_ARCLEN>(p, s);
+    if constexpr (PREC == P_F64)
+      return p.weights == W_JP ? launch_one<PREC, 2, W_JP>(p, s) : launch_one<PREC, 2, W_ARCLEN>(p, s);
+    else
+      return (int)cudaErrorInvalidValue;
   }
   return p.weights == W_JP ? launch_one<PREC, 1, W_JP>(p, s) : launch_one<PREC, 1, W_ARCLEN>(p, s);
 }
