@@ -116,7 +116,6 @@ struct Geo2D {
 };
 static_assert(Geo2D::SW == kBox2DW && Geo2D::SH == kBox2DH, "TMA box must match the tile halo");
 
-// Per-tile values prepared by thread 0 when the tile's loads are issued.
 // Everything a tile needs from its instance, gathered by thread 0 into shared memory when the
 // tile is prepared (one tile ahead), so that the compute phase reads no instance data from
 // global memory.
@@ -372,62 +371,77 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
     }
     __syncthreads();
 
-    // ---- 3. nodes (colY, K*segY + q): Lax-Friedrichs Hamiltonian, RK combination, store
+    // ---- 3. nodes (colY, K*segY + q): Lax-Friedrichs Hamiltonian, RK combination, store; one
+    // unrolled loop per stage and per edge/interior tile, so that no node tests either
+    auto finish = [&](auto stage_c, auto edge_c) {
+      constexpr int ST = decltype(stage_c)::value;
+      constexpr bool EDGE = decltype(edge_c)::value;
 #pragma unroll
-    for (int q = 0; q < K; ++q) {
-      const float dmq = ym[q], dpq = yp[q];
-      const int y = K * segY + q;
-      const int gi = tx0 + colY, gj = ty0 + y;
-      const bool inside = !edge || (gi < nx && gj < ny);
-      const float2 u = su[y * SUP + colY];
-      const float xn = fmaf((float)gi, d.dx, d.xlo), yn = fmaf((float)gj, d.dy, d.ylo);
-      float ax, ay;
-      ham.alpha(u.x, u.y, dmq, dpq, xn, yn, ax, ay);
-      const float aX = local_alpha ? ax : fax, aY = local_alpha ? ay : fay;
-      const float Hv = ham.value(0.5f * (u.y + u.x), 0.5f * (dpq + dmq), xn, yn);
-      const float L = fmaf(aX * 0.5f, u.y - u.x, fmaf(aY * 0.5f, dpq - dmq, -Hv));
-      if (inside) {
-        if (!isfinite(L)) bad = true;   // L depends on all four one-sided derivatives
-        amx = fmaxf(amx, ax);
-        amy = fmaxf(amy, ay);
-      }
-      if (p.stage == 0 || !inside) continue;
-      const int sidx = (y + 3) * SW + colY + 4;
-      const size_t g = rbase + (size_t)(gj + GY) * p.pitch + gi + GX;
-      if (PREC == P_MIXED) {
-        if (p.stage == 3) {
-          const float dd = (2.0f / 3.0f) * fmaf(dtf, L, C[sidx]);
-          float h, l;
-          df_add(A[sidx], B[sidx], dd, h, l);
-          float *oh = reinterpret_cast<float *>(p.mix_hi[i_cur ^ 1]);
-          float *ol = reinterpret_cast<float *>(p.mix_lo[i_cur ^ 1]);
-          if (edge) {
-            store_node<float, 2>(oh + rbase, p.pitch, nx, ny, d.bc, gi, gj, h);
-            store_node<float, 2>(ol + rbase, p.pitch, nx, ny, d.bc, gi, gj, l);
+      for (int q = 0; q < K; ++q) {
+        const float dmq = ym[q], dpq = yp[q];
+        const int y = K * segY + q;
+        const int gi = tx0 + colY, gj = ty0 + y;
+        const bool inside = !EDGE || (gi < nx && gj < ny);
+        const float2 u = su[y * SUP + colY];
+        const float xn = fmaf((float)gi, d.dx, d.xlo), yn = fmaf((float)gj, d.dy, d.ylo);
+        float ax, ay;
+        ham.alpha(u.x, u.y, dmq, dpq, xn, yn, ax, ay);
+        const float aX = local_alpha ? ax : fax, aY = local_alpha ? ay : fay;
+        const float Hv = ham.value(0.5f * (u.y + u.x), 0.5f * (dpq + dmq), xn, yn);
+        const float L = fmaf(aX * 0.5f, u.y - u.x, fmaf(aY * 0.5f, dpq - dmq, -Hv));
+        if (inside) {
+          if (!isfinite(L)) bad = true;   // L depends on all four one-sided derivatives
+          amx = fmaxf(amx, ax);
+          amy = fmaxf(amy, ay);
+        }
+        if (ST == 0 || !inside) continue;
+        const int sidx = (y + 3) * SW + colY + 4;
+        const size_t g = rbase + (size_t)(gj + GY) * p.pitch + gi + GX;
+        if (PREC == P_MIXED) {
+          if (ST == 3) {
+            const float dd = (2.0f / 3.0f) * fmaf(dtf, L, C[sidx]);
+            float h, l;
+            df_add(A[sidx], B[sidx], dd, h, l);
+            float *oh = reinterpret_cast<float *>(p.mix_hi[i_cur ^ 1]);
+            float *ol = reinterpret_cast<float *>(p.mix_lo[i_cur ^ 1]);
+            if (EDGE) {
+              store_node<float, 2>(oh + rbase, p.pitch, nx, ny, d.bc, gi, gj, h);
+              store_node<float, 2>(ol + rbase, p.pitch, nx, ny, d.bc, gi, gj, l);
+            } else {
+              oh[g] = h;
+              ol[g] = l;
+            }
           } else {
-            oh[g] = h;
-            ol[g] = l;
+            const float dd = (ST == 1) ? dtf * L : 0.25f * fmaf(dtf, L, C[sidx]);
+            float *o = reinterpret_cast<float *>(p.out0);
+            if (EDGE) store_node<float, 2>(o + rbase, p.pitch, nx, ny, d.bc, gi, gj, dd);
+            else o[g] = dd;
           }
         } else {
-          const float dd = (p.stage == 1) ? dtf * L : 0.25f * fmaf(dtf, L, C[sidx]);
+          const float src = A[sidx];
+          float outv;
+          if (ST == 1) {
+            outv = fmaf(dtf, L, src);
+          } else if (ST == 2) {
+            outv = fmaf(0.75f, B[sidx], 0.25f * fmaf(dtf, L, src));
+          } else {
+            outv = fmaf(1.0f / 3.0f, B[sidx], (2.0f / 3.0f) * fmaf(dtf, L, src));
+          }
           float *o = reinterpret_cast<float *>(p.out0);
-          if (edge) store_node<float, 2>(o + rbase, p.pitch, nx, ny, d.bc, gi, gj, dd);
-          else o[g] = dd;
+          if (EDGE) store_node<float, 2>(o + rbase, p.pitch, nx, ny, d.bc, gi, gj, outv);
+          else o[g] = outv;
         }
-      } else {
-        const float src = A[sidx];
-        float outv;
-        if (p.stage == 1) {
-          outv = fmaf(dtf, L, src);
-        } else if (p.stage == 2) {
-          outv = fmaf(0.75f, B[sidx], 0.25f * fmaf(dtf, L, src));
-        } else {
-          outv = fmaf(1.0f / 3.0f, B[sidx], (2.0f / 3.0f) * fmaf(dtf, L, src));
-        }
-        float *o = reinterpret_cast<float *>(p.out0);
-        if (edge) store_node<float, 2>(o + rbase, p.pitch, nx, ny, d.bc, gi, gj, outv);
-        else o[g] = outv;
       }
+    };
+    auto finish_stage = [&](auto stage_c) {
+      if (edge) finish(stage_c, std::true_type{});
+      else finish(stage_c, std::false_type{});
+    };
+    switch (p.stage) {
+      case 0: finish_stage(std::integral_constant<int, 0>{}); break;
+      case 1: finish_stage(std::integral_constant<int, 1>{}); break;
+      case 2: finish_stage(std::integral_constant<int, 2>{}); break;
+      default: finish_stage(std::integral_constant<int, 3>{}); break;
     }
 
     // ---- when the next tile of this CTA belongs to another instance (or there is none), fold the
