@@ -349,7 +349,6 @@ void copier_main(alw_server *s) {
         return;
       }
       std::lock_guard<std::mutex> lk(s->mu);
-      if (r->status == ALW_OK) r->status = ALW_OK;
       r->t_done = now_s();
       r->done = 1;
       s->rows.give(r->row_off, r->rows);
