@@ -419,6 +419,16 @@ def run_ours(args):
         "fp32": {"achieved_tflops": algo["flops"] * pts * 3 / (stage_total_ms * 1e-3) / 1e12,
                  "peak_tflops": SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12},
     }
+    # instruction issue, the unit this kernel saturates: thread instructions per node and stage from the
+    # same ncu capture as the traffic (arc length, MIXED) against 4 schedulers x 32 lanes per SM and clock
+    if traffic and traffic.get("thread_instructions_per_point_stage") and \
+            (args.weights, args.precision) == ("arclength", "mixed"):
+        inst = traffic["thread_instructions_per_point_stage"]
+        achieved = sum(inst) * pts / (stage_total_ms * 1e-3) / 1e12
+        peak = SM_COUNT * 4 * 32 * SM_MAX_MHZ * 1e6 / 1e12
+        roof["issue"] = {"achieved_tinst_s": achieved, "peak_tinst_s": peak, "frac": achieved / peak,
+                         "peak_source": f"derived: {SM_COUNT} SMs x 4 schedulers x 32 lanes x {SM_MAX_MHZ:.0f} MHz",
+                         "thread_instructions_per_point_stage": inst}
     cpu = None
     if not args.no_cpu and ws >= 1:
         import oracle
