@@ -115,3 +115,16 @@ def test_example11_float_paths_track_fp64(precision):
             s.step_to(0.5)
             out[prec] = s.get_phi()
     assert np.max(np.abs(out[precision] - out["fp64"])) < 1e-4
+
+
+@pytest.mark.parametrize("weights", ["arclength", "jp"])
+@pytest.mark.parametrize("name", ["ex10_sin2d", "ex12_eikonal2d"])
+def test_examples_10_12_at_paper_size_match_oracle(name, weights):
+    # Example 10 (sin(p+q), pi(|y|-|x|), linear extrapolation, t = 1) and Example 12 (Eikonal,
+    # [0, 1)^2 periodic, t = 0.6) on the paper's 80^2 grids, FP64, whole solves
+    pr = inputs.PROBLEMS[name]
+    n = 80
+    phi0, _ = inputs.initial(pr, n)
+    case = Case(2, n, n, pr.ham, bc=pr.bc, weights=weights, lo=pr.lo, hi=pr.hi, alpha_mode="default")
+    got, ref = _solve_both(case, phi0, pr.t_final)
+    assert rel_err(got, ref) <= FP64_TOL
