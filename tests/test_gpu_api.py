@@ -1,6 +1,7 @@
 """C-ABI behaviour on the GPU: checkpoint/resume, error paths, full-size sampled
 parity in the configuration bench.py times, and 1D / boundary workloads."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -137,19 +138,31 @@ def test_riemann_linextrap_mixed_vs_fp64_gpu():
     assert np.max(np.abs(out["mixed"] - out["fp64"])) < 1e-4
 
 
-def test_gpu_reproduces_table3_orders():
-    # FP64 GPU solve of Example 3 with dt ~ dx^{5/3}: errors within 2x of Table 3 at 40^2 and 80^2
+def _paper_table(name):
+    rows = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", name)):
+        if line.startswith("#") or not line.strip():
+            continue
+        v = line.split()
+        rows[int(v[0])] = {"arclength": float(v[1]), "jp": float(v[3])}   # L-infinity columns
+    return rows
+
+
+@pytest.mark.parametrize("weights", ["arclength", "jp"])
+@pytest.mark.parametrize("ham,table", [("burgers2d", "table3_ex3_burgers2d.txt"),
+                                       ("negcos2d", "table4_ex4_negcos2d.txt")])
+def test_gpu_reproduces_tables_3_4(ham, table, weights):
+    # FP64 GPU solves of Examples 3 and 4 with dt ~ dx^{5/3}: L-infinity errors against the exact
+    # solution within 2x of the paper's Tables 3 and 4 from 40^2 to 320^2
     import exact
 
+    tab = _paper_table(table)
     tf = 0.5 / math.pi**2
-    res = {}
-    for n in (40, 80):
+    for n in (40, 80, 160, 320):
         x, dx = inputs.axis(n, -2.0, 2.0, "periodic")
-        case = Case(2, n, n, "burgers2d", lo=-2.0, hi=2.0, dt_mode="dx53")
+        case = Case(2, n, n, ham, weights=weights, lo=-2.0, hi=2.0, dt_mode="dx53")
         with case.solver() as s:
             s.set_phi0(inputs.phi0_negcos_diag_2d(x, x))
             s.step_to(tf)
-            e = np.abs(s.get_phi() - exact.negcos_diag_2d("burgers2d", x, x, tf))
-        res[n] = e.max()
-    assert 1.43e-4 / 2 < res[40] < 1.43e-4 * 2
-    assert 6.34e-6 / 2 < res[80] < 6.34e-6 * 2
+            e = np.abs(s.get_phi() - exact.negcos_diag_2d(ham, x, x, tf)).max()
+        assert tab[n][weights] / 2 < e < tab[n][weights] * 2, (n, e, tab[n][weights])
