@@ -166,3 +166,24 @@ def test_gpu_reproduces_tables_3_4(ham, table, weights):
             s.step_to(tf)
             e = np.abs(s.get_phi() - exact.negcos_diag_2d(ham, x, x, tf)).max()
         assert tab[n][weights] / 2 < e < tab[n][weights] * 2, (n, e, tab[n][weights])
+
+
+@pytest.mark.parametrize("weights", ["arclength", "jp"])
+@pytest.mark.parametrize("ham,table,tf,factor", [("advect1d", "table1_ex1_advection.txt", 2.0, 1.6),
+                                                 ("negcos1d", "table2_ex2_negcos1d.txt", 0.5 / math.pi**2, 1.3)])
+def test_gpu_reproduces_tables_1_2(ham, table, tf, factor, weights):
+    # FP64 GPU solves of Examples 1 and 2 (node-local alpha, dt ~ dx^{5/3}): L-infinity errors against
+    # the exact solution within the factors the oracle meets, from N = 20 to 320
+    import exact
+
+    tab = _paper_table(table)
+    for n in (20, 40, 80, 160, 320):
+        x, dx = inputs.axis(n, -1.0, 1.0, "periodic")
+        case = Case(1, n, 1, ham, weights=weights, alpha_mode="local_lagged", dt_mode="dx53")
+        with case.solver() as s:
+            s.set_phi0(inputs.phi0_negcos_1d(x))
+            s.step_to(tf)
+            got = s.get_phi()
+        ex = -np.cos(np.pi * (x - tf)) if ham == "advect1d" else exact.negcos_1d(ham, x, tf)
+        e = np.abs(got - ex).max()
+        assert tab[n][weights] / factor < e < tab[n][weights] * factor, (n, e, tab[n][weights])
