@@ -306,6 +306,48 @@ def bench_serving(args, stream, rate):
             "budget_gb": args.serve_budget_gb}
 
 
+def run_sizes_report(args):
+    """Device throughput of one RK3 step by grid size and precision (one JSON line).
+
+    Example 3 (Burgers, periodic) on 400^2, 2048^2 and 8192^2 and Example 10 (sin(p+q), linear
+    extrapolation) on 1024^2 and 4096^2, in MIXED, FP32 and FP64, arc-length weights: CUDA events on
+    the solver's stream around a timed run of RK3 steps after warm-up steps."""
+    import torch
+
+    from paper_1909_13263_gb300 import inputs, native
+
+    native.load()
+    native.use_torch_allocator(True)
+    stream = torch.cuda.Stream()
+    out = {"report": "sizes", "unit": "point-updates/s", "weights": args.weights}
+    cases = [("ex3_burgers2d", n, "burgers2d", "periodic", -2.0, 2.0) for n in (400, 2048, 8192)]
+    cases += [("ex10_sin2d_linextrap", n, "sin2d", "linextrap", -1.0, 1.0) for n in (1024, 4096)]
+    for name, n, ham, bc, lo, hi in cases:
+        x, _ = inputs.axis(n, lo, hi, bc)
+        phi0 = inputs.phi0_negcos_diag_2d(x, x) if ham == "burgers2d" else inputs.phi0_riemann_2d(x, x)
+        row = {}
+        for prec in ("mixed", "fp32", "fp64"):
+            with torch.cuda.stream(stream):
+                with native.Solver(dim=2, nx=n, ny=n, bc=bc, xlo=lo, xhi=hi, ylo=lo, yhi=hi, ham=ham,
+                                   precision=prec, weights=args.weights, stream=stream) as s:
+                    s.set_phi0(phi0)
+                    s.advance(3)
+                    torch.cuda.synchronize()
+                    # about 0.3 s of timed work (at least 3 steps)
+                    rate_guess = {"fp64": 2.0e8}.get(prec, 2.0e10)
+                    steps = max(3, min(2000, int(0.3 * rate_guess / (n * n))))
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    s.advance(steps)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms = e0.elapsed_time(e1) / steps
+            row[prec] = {"ms_per_step": ms, "point_updates_per_s": n * n / (ms * 1e-3), "steps": steps}
+        out[f"{name}_{n}sq"] = row
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -558,7 +600,7 @@ def main():
     ap.add_argument("--serve-round-tiles", type=int, default=None,
                     help="tile limit of a server round (default: the server's own, four kernel waves; 0: none)")
     ap.add_argument("--serve-rates", type=str, default="", help="comma-separated arrival rates (a sweep)")
-    ap.add_argument("--report", choices=["", "precision"], default="",
+    ap.add_argument("--report", choices=["", "precision", "sizes"], default="",
                     help="precision: errors of the float paths against FP64 and the exact solution")
     ap.add_argument("--report-ex3-sizes", type=str, default="400,2048",
                     help="precision report: grid sides of Example 3 (comma-separated)")
@@ -573,6 +615,8 @@ def main():
         return run_reference(args)
     if args.report == "precision":
         return run_precision_report(args)
+    if args.report == "sizes":
+        return run_sizes_report(args)
     return run_ours(args)
 
 
