@@ -43,7 +43,7 @@ FP32_LANES_PER_SM = 128
 # algorithmic work of one 2D node in one stage (arc-length weights, Burgers H):
 # per direction 3 F evaluations (rsqrt + lg2), 3 interval means (1 reciprocal each),
 # 2 weight sets (1 reciprocal each) -> 11 MUFU ops; FP32 flops ~107 per direction
-# plus ~33 for alpha, H-hat and the RK combination (see the design doc for the count)
+# plus ~33 for alpha, H-hat and the RK combination; bytes: each array read or written once per stage
 ALGO = {
     ("arclength", "mixed"): {"mufu": 22, "flops": 250, "bytes": (12, 16, 20)},
     ("arclength", "fp32"): {"mufu": 22, "flops": 240, "bytes": (8, 12, 12)},
