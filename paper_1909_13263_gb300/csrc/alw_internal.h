@@ -69,7 +69,7 @@ constexpr int GY = 3;
 
 // Tile shapes per variant.
 template <int PREC> struct Tile;
-template <> struct Tile<P_F64> { static constexpr int TX = 64, TY = 16, K = 8; };
+template <> struct Tile<P_F64> { static constexpr int TX = 32, TY = 16, K = 4; };
 template <> struct Tile<P_F32> { static constexpr int TX = 64, TY = 32, K = 8; };
 template <> struct Tile<P_MIXED> { static constexpr int TX = 64, TY = 32, K = 8; };
 constexpr int TX1D = 256;       // 1D tile width (one row)
