@@ -310,8 +310,9 @@ def run_sizes_report(args):
     """Device throughput of one RK3 step by grid size and precision (one JSON line).
 
     Example 3 (Burgers, periodic) on 400^2, 2048^2 and 8192^2 and Example 10 (sin(p+q), linear
-    extrapolation) on 1024^2 and 4096^2, in MIXED, FP32 and FP64, arc-length weights: CUDA events on
-    the solver's stream around a timed run of RK3 steps after warm-up steps."""
+    extrapolation) on 1024^2 and 4096^2, in MIXED, FP32 and FP64, plus FP64 Example 3 from 80^2 to
+    1024^2, arc-length weights: CUDA events on the solver's stream around a timed run of RK3 steps
+    after warm-up steps."""
     import torch
 
     from paper_1909_13263_gb300 import inputs, native
@@ -344,6 +345,25 @@ def run_sizes_report(args):
                     ms = e0.elapsed_time(e1) / steps
             row[prec] = {"ms_per_step": ms, "point_updates_per_s": n * n / (ms * 1e-3), "steps": steps}
         out[f"{name}_{n}sq"] = row
+    # FP64 at the paper's grid sizes (Example 3)
+    fp64 = {}
+    for n in (80, 160, 320, 640, 1024):
+        x, _ = inputs.axis(n, -2.0, 2.0, "periodic")
+        with torch.cuda.stream(stream):
+            with native.Solver(dim=2, nx=n, ny=n, xlo=-2.0, xhi=2.0, ylo=-2.0, yhi=2.0, ham="burgers2d",
+                               precision="fp64", weights=args.weights, stream=stream) as s:
+                s.set_phi0(inputs.phi0_negcos_diag_2d(x, x))
+                s.advance(3)
+                torch.cuda.synchronize()
+                steps = max(3, min(400, int(0.3 * 2.0e8 / (n * n))))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.advance(steps)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / steps
+        fp64[f"{n}sq"] = {"ms_per_step": ms, "point_updates_per_s": n * n / (ms * 1e-3), "steps": steps}
+    out["ex3_burgers2d_fp64_paper_sizes"] = fp64
     print(json.dumps(out), flush=True)
     return 0
 
