@@ -4,10 +4,10 @@
 
 namespace alw {
 
-template <int PREC, int DIM, int W>
+template <int PREC, int DIM, int W, bool SMALL = false>
 static int launch_one(const StageParams &p, cudaStream_t stream) {
-  using Sh = Shape<PREC, DIM>;
-  auto kern = stage_kernel<PREC, DIM, W>;
+  using Sh = Shape<PREC, DIM, SMALL>;
+  auto kern = stage_kernel<PREC, DIM, W, SMALL>;
   const size_t smem = Sh::smem_bytes();
   static bool configured = false;   // attribute is per function; setting it twice is harmless
   if (!configured) {
@@ -26,9 +26,11 @@ template <int PREC>
 static int launch_stage_impl(const StageParams &p, void *stream) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (p.dim == 2) {
-    if constexpr (PREC == P_F64)
+    if constexpr (PREC == P_F64) {
+      if (p.small_tiles)
+        return p.weights == W_JP ? launch_one<PREC, 2, W_JP, true>(p, s) : launch_one<PREC, 2, W_ARCLEN, true>(p, s);
       return p.weights == W_JP ? launch_one<PREC, 2, W_JP>(p, s) : launch_one<PREC, 2, W_ARCLEN>(p, s);
-    else
+    } else
       return (int)cudaErrorInvalidValue;
   }
   return p.weights == W_JP ? launch_one<PREC, 1, W_JP>(p, s) : launch_one<PREC, 1, W_ARCLEN>(p, s);

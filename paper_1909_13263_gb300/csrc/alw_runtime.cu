@@ -143,6 +143,7 @@ struct alw_solver {
   cudaGraphExec_t g_adv = nullptr;
   bool has_phi = false;
   bool use2d = false;       // persistent TMA kernel (2D float variants)
+  bool small_tiles = false; // FP64 2D: 16 x 16 tiles for grids that would not fill the GPU otherwise
   CUtensorMap maps[6];      // tensor maps of the padded arrays (see Stage2DParams)
 
   void *alloc(size_t bytes) {
@@ -219,6 +220,7 @@ StageParams make_params(const alw_solver *s, int stage, int src_of, int loop_mod
   p.pitch = s->pitch;
   p.tiles_x = s->tiles_x;
   p.tiles_y = s->tiles_y;
+  p.small_tiles = s->small_tiles ? 1 : 0;
   p.dim = s->dim;
   p.bc = s->grid.bc;
   p.ham = s->ham.kind;
@@ -469,7 +471,17 @@ alw_status alw_create(const alw_grid *grid, const alw_hamiltonian *ham, const al
   s->dy = grid->dim == 2 ? (grid->yhi - grid->ylo) / (per ? grid->ny : grid->ny - 1) : s->dx;
   s->lx = scheme->dt_mode == ALW_DT_DX53 ? std::pow(s->dx, 5.0 / 3.0) : s->dx;
   s->ly = scheme->dt_mode == ALW_DT_DX53 ? std::pow(s->dy, 5.0 / 3.0) : s->dy;
-  const int tx = tile_x(s->prec, s->dim), ty = tile_y(s->prec, s->dim);
+  int tx = tile_x(s->prec, s->dim), ty = tile_y(s->prec, s->dim);
+  if (s->dim == 2 && s->prec == P_F64) {
+    // one FP64 tile keeps an SM busy for a long time: where the default tiles would not give every SM
+    // two, 16 x 16 tiles spread the grid over four times as many CTAs
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long t = (long long)((s->nx + tx - 1) / tx) * ((s->ny + ty - 1) / ty);
+    s->small_tiles = sms > 0 && t < 2LL * sms;
+    if (s->small_tiles) tx = ty = 16;
+  }
   s->tiles_x = (s->nx + tx - 1) / tx;
   s->tiles_y = (s->ny + ty - 1) / ty;
   s->pitch = s->tiles_x * tx + 2 * GX;

@@ -9,10 +9,11 @@ template <> struct Types<P_F64> { using S = double; using C = double; };
 template <> struct Types<P_F32> { using S = float; using C = float; };
 template <> struct Types<P_MIXED> { using S = float; using C = float; };
 
-template <int PREC, int DIM> struct Shape {
-  static constexpr int TX = (DIM == 2) ? Tile<PREC>::TX : TX1D;
-  static constexpr int TY = (DIM == 2) ? Tile<PREC>::TY : 1;
-  static constexpr int K = (DIM == 2) ? Tile<PREC>::K : K1D;
+// SMALL: 16 x 16 tiles (FP64 2D grids too small to fill the GPU with the default tiles).
+template <int PREC, int DIM, bool SMALL = false> struct Shape {
+  static constexpr int TX = (DIM == 2) ? (SMALL ? 16 : Tile<PREC>::TX) : TX1D;
+  static constexpr int TY = (DIM == 2) ? (SMALL ? 16 : Tile<PREC>::TY) : 1;
+  static constexpr int K = (DIM == 2) ? (SMALL ? 4 : Tile<PREC>::K) : K1D;
   static constexpr int NT = (TX / K) * TY;          // threads per CTA
   static constexpr int SW = TX + 8;                 // smem row: GX halo on each side
   static constexpr int SH = (DIM == 2) ? TY + 6 : 1;
@@ -23,11 +24,11 @@ template <int PREC, int DIM> struct Shape {
   }
 };
 
-template <int PREC, int DIM, int WEIGHTS>
-__global__ void __launch_bounds__(Shape<PREC, DIM>::NT) stage_kernel(const StageParams p) {
+template <int PREC, int DIM, int WEIGHTS, bool SMALL>
+__global__ void __launch_bounds__(Shape<PREC, DIM, SMALL>::NT) stage_kernel(const StageParams p) {
   using S = typename Types<PREC>::S;
   using C = typename Types<PREC>::C;
-  using Sh = Shape<PREC, DIM>;
+  using Sh = Shape<PREC, DIM, SMALL>;
   constexpr int TX = Sh::TX, TY = Sh::TY, K = Sh::K, NT = Sh::NT, SW = Sh::SW, SH = Sh::SH;
 
   DevState *st = p.state;
