@@ -290,7 +290,9 @@ alw_status alw_server_set_round_steps(alw_server *s, int32_t steps);
  * admission order while the round holds at most `tiles` tiles (64 x 32 nodes each)
  * in total, and instances of at most 32 tiles always join.  Large solves thus run
  * in arrival order with the small ones beside them.  0 = no limit (every resident
- * instance in every round).  Default: four waves of the persistent stage kernel. */
+ * instance in every round).  Default: four waves of the persistent stage kernel.  Under load
+ * the limit grows to half of the resident instances' tiles, so that many waiting instances
+ * share fuller launches and fewer rounds. */
 alw_status alw_server_set_round_tiles(alw_server *s, int32_t tiles);
 /* Queue a solve (host_phi0 copied); req_id receives its id. */
 alw_status alw_server_submit(alw_server *s, const alw_grid *grid, const alw_hamiltonian *ham, const double *host_phi0,

@@ -390,6 +390,13 @@ void worker_main(alw_server *s) {
     // members of this round, oldest first: the oldest always; the others while the round's
     // tiles stay within the limit, and small instances always.  Large solves then run in
     // arrival order (as one at a time would), with the small ones beside them.
+    // under load the limit grows to half of the resident tiles: fuller launches and fewer rounds
+    // when many instances wait, arrival order when few do
+    if (tile_limit > 0) {
+      long long resident = 0;
+      for (Request *r : active) resident += s->h_inst[r->slot].ntiles;
+      tile_limit = (int)std::max<long long>(tile_limit, resident / 2);
+    }
     round.clear();
     long long round_tiles = 0;
     bool any_new = false;
