@@ -47,7 +47,7 @@ struct StageParams {
   double cfl, lx, ly;    // dt = cfl / (ax/lx + ay/ly)
   double alpha_fixed[2];
   double dt_value;       // LOOP_STAGE: the dt of this stage
-  int small_tiles;       // FP64 2D: 16 x 16 tiles (layout and kernel variant) instead of the default
+  int small_tiles;       // FP64 2D: 0 default tiles; 16 x 16 tiles with 4-node (1) or 2-node (2) segments
   // buffers: padded arrays whose interior origin is at row GY, column GX
   const void *src0, *src1, *src2;  // stencil source (F64/F32: src0; MIXED: hi, lo, delta or null)
   const void *base0, *base1;       // phi^n at the node (F64/F32: base0; MIXED: hi, lo; stage>=2)

@@ -4,7 +4,7 @@
 
 namespace alw {
 
-template <int PREC, int DIM, int W, bool SMALL = false>
+template <int PREC, int DIM, int W, int SMALL = 0>
 static int launch_one(const StageParams &p, cudaStream_t stream) {
   using Sh = Shape<PREC, DIM, SMALL>;
   auto kern = stage_kernel<PREC, DIM, W, SMALL>;
@@ -27,8 +27,10 @@ static int launch_stage_impl(const StageParams &p, void *stream) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (p.dim == 2) {
     if constexpr (PREC == P_F64) {
-      if (p.small_tiles)
-        return p.weights == W_JP ? launch_one<PREC, 2, W_JP, true>(p, s) : launch_one<PREC, 2, W_ARCLEN, true>(p, s);
+      if (p.small_tiles == 2)
+        return p.weights == W_JP ? launch_one<PREC, 2, W_JP, 2>(p, s) : launch_one<PREC, 2, W_ARCLEN, 2>(p, s);
+      if (p.small_tiles == 1)
+        return p.weights == W_JP ? launch_one<PREC, 2, W_JP, 1>(p, s) : launch_one<PREC, 2, W_ARCLEN, 1>(p, s);
       return p.weights == W_JP ? launch_one<PREC, 2, W_JP>(p, s) : launch_one<PREC, 2, W_ARCLEN>(p, s);
     } else
       return (int)cudaErrorInvalidValue;

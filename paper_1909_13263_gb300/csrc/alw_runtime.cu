@@ -143,7 +143,7 @@ struct alw_solver {
   cudaGraphExec_t g_adv = nullptr;
   bool has_phi = false;
   bool use2d = false;       // persistent TMA kernel (2D float variants)
-  bool small_tiles = false; // FP64 2D: 16 x 16 tiles for grids that would not fill the GPU otherwise
+  int small_tiles = 0;      // FP64 2D: 16 x 16 tiles for grids that would not fill the GPU otherwise (1, 2)
   CUtensorMap maps[6];      // tensor maps of the padded arrays (see Stage2DParams)
 
   void *alloc(size_t bytes) {
@@ -220,7 +220,7 @@ StageParams make_params(const alw_solver *s, int stage, int src_of, int loop_mod
   p.pitch = s->pitch;
   p.tiles_x = s->tiles_x;
   p.tiles_y = s->tiles_y;
-  p.small_tiles = s->small_tiles ? 1 : 0;
+  p.small_tiles = s->small_tiles;
   p.dim = s->dim;
   p.bc = s->grid.bc;
   p.ham = s->ham.kind;
@@ -479,8 +479,12 @@ alw_status alw_create(const alw_grid *grid, const alw_hamiltonian *ham, const al
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long t = (long long)((s->nx + tx - 1) / tx) * ((s->ny + ty - 1) / ty);
-    s->small_tiles = sms > 0 && t < 2LL * sms;
-    if (s->small_tiles) tx = ty = 16;
+    if (sms > 0 && t < 2LL * sms) {
+      // fewer 16 x 16 tiles than SMs: 2-node segments, twice the threads per tile
+      const long long t16 = (long long)((s->nx + 15) / 16) * ((s->ny + 15) / 16);
+      s->small_tiles = t16 < sms ? 2 : 1;
+      tx = ty = 16;
+    }
   }
   s->tiles_x = (s->nx + tx - 1) / tx;
   s->tiles_y = (s->ny + ty - 1) / ty;

@@ -9,11 +9,13 @@ template <> struct Types<P_F64> { using S = double; using C = double; };
 template <> struct Types<P_F32> { using S = float; using C = float; };
 template <> struct Types<P_MIXED> { using S = float; using C = float; };
 
-// SMALL: 16 x 16 tiles (FP64 2D grids too small to fill the GPU with the default tiles).
-template <int PREC, int DIM, bool SMALL = false> struct Shape {
+// SMALL (FP64 2D grids too small to fill the GPU with the default tiles): 16 x 16 tiles with 4-node
+// sweep segments (SMALL = 1), or 2-node segments (SMALL = 2: twice the threads per tile, for grids
+// whose 16 x 16 tiles are fewer than the SMs).
+template <int PREC, int DIM, int SMALL = 0> struct Shape {
   static constexpr int TX = (DIM == 2) ? (SMALL ? 16 : Tile<PREC>::TX) : TX1D;
   static constexpr int TY = (DIM == 2) ? (SMALL ? 16 : Tile<PREC>::TY) : 1;
-  static constexpr int K = (DIM == 2) ? (SMALL ? 4 : Tile<PREC>::K) : K1D;
+  static constexpr int K = (DIM == 2) ? (SMALL == 2 ? 2 : SMALL == 1 ? 4 : Tile<PREC>::K) : K1D;
   static constexpr int NT = (TX / K) * TY;          // threads per CTA
   static constexpr int SW = TX + 8;                 // smem row: GX halo on each side
   static constexpr int SH = (DIM == 2) ? TY + 6 : 1;
@@ -24,7 +26,7 @@ template <int PREC, int DIM, bool SMALL = false> struct Shape {
   }
 };
 
-template <int PREC, int DIM, int WEIGHTS, bool SMALL>
+template <int PREC, int DIM, int WEIGHTS, int SMALL>
 __global__ void __launch_bounds__(Shape<PREC, DIM, SMALL>::NT) stage_kernel(const StageParams p) {
   using S = typename Types<PREC>::S;
   using C = typename Types<PREC>::C;
