@@ -282,27 +282,31 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
   int run_tiles = 0;
   // thread 0: work-list entry of the tile after next, loaded one tile ahead of its use
   int e_ahead = (batch && tid == 0 && (int)(blockIdx.x + gridDim.x) < ntiles) ? prm.tiles[blockIdx.x + gridDim.x] : 0;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
-    const int buf = k & 1;
-    const int next = t + gridDim.x;
+  // thread 0, once every thread is past the previous tile's reads of buffer buf ^ 1 and of
+  // s_info[buf ^ 1]: prepare the next tile into that buffer
+  auto prepare_next = [&](int next, int buf) {
     if (tid == 0 && next < ntiles) {
       fence_proxy_async_smem();
       prepare(next, e_ahead, buf ^ 1);
       const int after = next + (int)gridDim.x;
       e_ahead = (batch && after < ntiles) ? prm.tiles[after] : 0;
     }
+  };
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+    const int buf = k & 1;
+    const int next = t + gridDim.x;
     const int i_inst = s_info[buf].inst, i_skip = s_info[buf].skip, i_cur = s_info[buf].cur;
     if (i_skip) {
+      __syncthreads();
+      prepare_next(next, buf);
       __syncthreads();
       continue;
     }
     const bool ok = mbar_wait_bounded(&bars[buf], (phase >> buf) & 1u);
     if (__syncthreads_or(!ok)) {
-      // a tile load never completed: flag the instance, let the other in-flight load land, stop
-      if (tid == 0) {
-        atomicOr(&s_info[buf].st->err, 2);
-        if (next < ntiles && !s_info[buf ^ 1].skip) mbar_wait_bounded(&bars[buf ^ 1], (phase >> (buf ^ 1)) & 1u);
-      }
+      // a tile load never completed: flag the instance and stop (the next tile's load is issued
+      // only after this wait, so no other load is in flight)
+      if (tid == 0) atomicOr(&s_info[buf].st->err, 2);
       __syncthreads();
       return;
     }
@@ -349,6 +353,9 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
     if (has_delta) diff_pass(std::true_type{});
     else diff_pass(std::false_type{});
     __syncthreads();
+    // every thread has finished the previous tile (its finish loop read buffer buf ^ 1), so the next
+    // tile's load can go there; the barrier after the sweeps publishes s_info[buf ^ 1]
+    prepare_next(next, buf);
 
     const bool edge = (tx0 < 3) || (tx0 + TX > nx - 3) || (ty0 < 3) || (ty0 + TY > ny - 3);
     const int colY = ((warp & 1) << 5) + lane, segY = warp >> 1;
@@ -449,7 +456,9 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
     ++run_tiles;
     const bool more = next < ntiles;
     if (more && !s_info[buf ^ 1].skip && s_info[buf ^ 1].inst == i_inst) {
-      __syncthreads();  // raw[buf], dX, dY, su are free for the next tile
+      // no barrier: the next tile's differences pass writes only dX and dY, which this tile read
+      // before the barrier after the sweeps; su and raw[buf] are rewritten only after the next
+      // tile's first barrier, which every thread reaches after finishing this tile
       continue;
     }
 #pragma unroll

@@ -39,6 +39,26 @@ __device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 vsplat(float x, float2) { return make_float2(x, x); }
 
+// Special-function-unit approximations in their flush-to-zero PTX forms (reciprocal square root,
+// base-2 logarithm, reciprocal).  No input here is subnormal -- 1 + u^2 >= 1, |u| + sqrt(1 + u^2) >= 1,
+// weight denominators >= 1e-24 -- except 1/h for a vanishing interval, whose quotient the trapezoid
+// branch discards, so the results equal those of the non-flushing forms.
+__device__ __forceinline__ float sfu_rsqrt(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float sfu_lg2(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float sfu_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 template <class V> struct Lanes;
 template <> struct Lanes<float> {
   static constexpr int n = 1;
@@ -62,12 +82,12 @@ __device__ __forceinline__ FValV<V> f_eval_v(V u) {
   const V t = vfma(u, u, vsplat(1.0f, u));
   V rs, lsg;
 #pragma unroll
-  for (int i = 0; i < LN::n; ++i) LN::at(rs, i) = rsqrtf(LN::get(t, i));
+  for (int i = 0; i < LN::n; ++i) LN::at(rs, i) = sfu_rsqrt(LN::get(t, i));
   r.s = vmul(t, rs);
   // |u| + s per lane (the absolute value is an operand modifier of the scalar add)
 #pragma unroll
   for (int i = 0; i < LN::n; ++i)
-    LN::at(lsg, i) = copysignf(__log2f(fabsf(LN::get(u, i)) + LN::get(r.s, i)), LN::get(u, i));
+    LN::at(lsg, i) = copysignf(sfu_lg2(fabsf(LN::get(u, i)) + LN::get(r.s, i)), LN::get(u, i));
   // asinh|u| = ln(|u| + sqrt(1+u^2)); absolute error of the base-2 log ~ 2^-22
   r.F = vfma(vsplat(0.693147180559945f, u), lsg, vmul(u, r.s));
   return r;
@@ -83,7 +103,7 @@ __device__ __forceinline__ V q_interval_v(V a, FValV<V> fa, V b, FValV<V> fb, V 
   const V thr = vmul(vsplat(0.015625f, h), ss);
   V rh;
 #pragma unroll
-  for (int i = 0; i < LN::n; ++i) LN::at(rh, i) = __fdividef(1.0f, LN::get(h, i));
+  for (int i = 0; i < LN::n; ++i) LN::at(rh, i) = sfu_rcp(LN::get(h, i));
   const V gd = vmul(dF, rh);
   V g;
 #pragma unroll
@@ -118,7 +138,7 @@ __device__ __forceinline__ V side_corr_v(V q0, V q1, V q2, V ta3, V tb2) {
   for (int i = 0; i < LN::n; ++i) {
     const float dn = LN::get(den, i);
     ok = ok && (dn < 1e30f);
-    LN::at(rd, i) = __fdividef(1.0f, dn);
+    LN::at(rd, i) = sfu_rcp(dn);
   }
   V out = vmul(num, rd);
   if (!ok) {
