@@ -46,29 +46,32 @@ template <> struct Ham2<H_BURGERS2D> {
   }
 };
 template <> struct Ham2<H_NEGCOS2D> {
-  __device__ __forceinline__ static float value(float p, float q, float, float) { return -__cosf(p + q + 1.0f); }
+  __device__ __forceinline__ static float value(float p, float q, float, float) { return -sfu_cos(p + q + 1.0f); }
   __device__ __forceinline__ static void alpha(float um, float up, float vm, float vp, float, float, float &ax,
                                                     float &ay) {
-    const float a = fabsf(__sinf(um + vm + 1.0f)), b = fabsf(__sinf(um + vp + 1.0f));
-    const float c = fabsf(__sinf(up + vm + 1.0f)), d = fabsf(__sinf(up + vp + 1.0f));
+    const float a = fabsf(sfu_sin(um + vm + 1.0f)), b = fabsf(sfu_sin(um + vp + 1.0f));
+    const float c = fabsf(sfu_sin(up + vm + 1.0f)), d = fabsf(sfu_sin(up + vp + 1.0f));
     ax = ay = fmaxf(fmaxf(a, b), fmaxf(c, d));
   }
 };
 template <> struct Ham2<H_SIN2D> {
-  __device__ __forceinline__ static float value(float p, float q, float, float) { return __sinf(p + q); }
+  __device__ __forceinline__ static float value(float p, float q, float, float) { return sfu_sin(p + q); }
   __device__ __forceinline__ static void alpha(float um, float up, float vm, float vp, float, float, float &ax,
                                                     float &ay) {
-    const float a = fabsf(__cosf(um + vm)), b = fabsf(__cosf(um + vp));
-    const float c = fabsf(__cosf(up + vm)), d = fabsf(__cosf(up + vp));
+    const float a = fabsf(sfu_cos(um + vm)), b = fabsf(sfu_cos(um + vp));
+    const float c = fabsf(sfu_cos(up + vm)), d = fabsf(sfu_cos(up + vp));
     ax = ay = fmaxf(fmaxf(a, b), fmaxf(c, d));
   }
 };
 template <> struct Ham2<H_EIKONAL2D> {
-  __device__ __forceinline__ static float value(float p, float q, float, float) { return sqrtf(fmaf(p, p, fmaf(q, q, 1.0f))); }
+  __device__ __forceinline__ static float value(float p, float q, float, float) {
+    const float t = fmaf(p, p, fmaf(q, q, 1.0f));   // >= 1
+    return t * sfu_rsqrt(t);
+  }
   __device__ __forceinline__ static void alpha(float um, float up, float vm, float vp, float, float, float &ax,
                                                     float &ay) {
-    const float r00 = rsqrtf(fmaf(um, um, fmaf(vm, vm, 1.0f))), r01 = rsqrtf(fmaf(um, um, fmaf(vp, vp, 1.0f)));
-    const float r10 = rsqrtf(fmaf(up, up, fmaf(vm, vm, 1.0f))), r11 = rsqrtf(fmaf(up, up, fmaf(vp, vp, 1.0f)));
+    const float r00 = sfu_rsqrt(fmaf(um, um, fmaf(vm, vm, 1.0f))), r01 = sfu_rsqrt(fmaf(um, um, fmaf(vp, vp, 1.0f)));
+    const float r10 = sfu_rsqrt(fmaf(up, up, fmaf(vm, vm, 1.0f))), r11 = sfu_rsqrt(fmaf(up, up, fmaf(vp, vp, 1.0f)));
     ax = fmaxf(fmaxf(fabsf(um) * r00, fabsf(um) * r01), fmaxf(fabsf(up) * r10, fabsf(up) * r11));
     ay = fmaxf(fmaxf(fabsf(vm) * r00, fabsf(vp) * r01), fmaxf(fabsf(vm) * r10, fabsf(vp) * r11));
   }
@@ -77,17 +80,15 @@ template <> struct Ham2<H_EIKONAL2D> {
 // Example 11 (optimal control): the only Hamiltonian that depends on the node position (x, y).
 template <> struct Ham2<H_OPTCTRL2D> {
   __device__ __forceinline__ static float value(float p, float q, float x, float y) {
-    float sx, cx, sy, cy;
-    __sincosf(x, &sx, &cx);
-    __sincosf(y, &sy, &cy);
+    const float sx = sfu_sin(x), cx = sfu_cos(x), sy = sfu_sin(y);
     // sin(y) p + (sin(x) + sign q) q - sin^2(y)/2 - (1 - cos x), with (sign q) q = |q|
     return fmaf(sy, p, fmaf(sx, q, fabsf(q))) - fmaf(0.5f * sy, sy, 1.0f - cx);
   }
   __device__ __forceinline__ static void alpha(float, float, float vm, float vp, float x, float y, float &ax,
                                                float &ay) {
     // H_p = sin y; H_q = sin x + sign q over [min v, max v], both signs when it contains q = 0
-    const float sx = __sinf(x), lo = fminf(vm, vp), hi = fmaxf(vm, vp);
-    ax = fabsf(__sinf(y));
+    const float sx = sfu_sin(x), lo = fminf(vm, vp), hi = fmaxf(vm, vp);
+    ax = fabsf(sfu_sin(y));
     ay = (lo <= 0.0f && hi >= 0.0f) ? fabsf(sx) + 1.0f : fabsf(sx + (lo > 0.0f ? 1.0f : -1.0f));
   }
 };

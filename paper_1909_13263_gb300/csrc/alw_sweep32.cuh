@@ -58,6 +58,18 @@ __device__ __forceinline__ float sfu_rcp(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
+// sine and cosine of the Hamiltonians (absolute error about 2^-20 for moderate arguments; a subnormal argument
+// gives 0 instead of itself)
+__device__ __forceinline__ float sfu_sin(float x) {
+  float r;
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float sfu_cos(float x) {
+  float r;
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 
 template <class V> struct Lanes;
 template <> struct Lanes<float> {
