@@ -7,13 +7,15 @@
 // and issues one TMA box per array (tile plus 3-node halo) into the other half
 // of a double buffer on an mbarrier -- while all threads compute the current
 // tile:
-//   1. differences pass: Delta^+ phi along x (dX) and y (dY) for every cell,
-//      combining the MIXED parts (hi + lo + delta) once per cell;
+//   1. differences pass: Delta^+ phi along x (dX) for every cell, combining
+//      the MIXED parts (hi + lo + delta) once per cell;
 //   2. both sweeps in one pass, packed two lanes per value (f32x2): each
 //      thread sweeps nodes 8w..8w+7 of row `lane` along x (warp w; the odd dX
 //      pitch makes these column-wise reads conflict-free) in lane .x and 8
-//      consecutive nodes of one column along y in lane .y; phi_x^-/+ go to
-//      shared memory, phi_y^-/+ stay in registers;
+//      consecutive nodes of one column along y in lane .y, whose differences
+//      it forms itself from the tile arrays (consecutive lanes read
+//      consecutive columns); phi_x^-/+ go to shared memory, phi_y^-/+ stay in
+//      registers;
 //   3. each thread forms, for its 8 column nodes, the Lax-Friedrichs
 //      Hamiltonian and the RK combination, and stores.
 // A CTA keeps running maxima of |dH/dp|, |dH/dq| over consecutive tiles of
@@ -109,10 +111,9 @@ struct Geo2D {
   static constexpr int SW = TX + 8, SH = TY + 6;        // TMA box (halo 4 columns / 3 rows each side)
   static constexpr int ARR = ((SH * SW + 31) / 32) * 32; // floats per array slot (128-byte multiple)
   static constexpr int DXW = TX + 5, DXP = 73;          // x differences: width, odd pitch
-  static constexpr int DYH = TY + 5;                    // y differences: rows
   static constexpr int SUP = TX + 1;                    // phi_x^-/+ pitch in float2
   template <int NARR> static constexpr size_t smem_bytes() {
-    return 128 + sizeof(float) * (size_t)(2 * NARR * ARR + TY * DXP + DYH * TX) + sizeof(float2) * (size_t)TY * SUP;
+    return 128 + sizeof(float) * (size_t)(2 * NARR * ARR + TY * DXP) + sizeof(float2) * (size_t)TY * SUP;
   }
 };
 static_assert(Geo2D::SW == kBox2DW && Geo2D::SH == kBox2DH, "TMA box must match the tile halo");
@@ -133,7 +134,7 @@ template <int PREC, int W, int H>
 __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_constant__ Stage2DParams prm) {
   constexpr int TX = Geo2D::TX, TY = Geo2D::TY, K = Geo2D::K, NT = Geo2D::NT;
   constexpr int SW = Geo2D::SW, SH = Geo2D::SH, ARR = Geo2D::ARR;
-  constexpr int DXW = Geo2D::DXW, DXP = Geo2D::DXP, DYH = Geo2D::DYH, SUP = Geo2D::SUP;
+  constexpr int DXW = Geo2D::DXW, DXP = Geo2D::DXP, SUP = Geo2D::SUP;
   constexpr int NARR = (PREC == P_MIXED) ? 3 : 2;
   const StageParams &p = prm.p;
   const bool batch = prm.insts != nullptr;
@@ -148,8 +149,7 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
   unsigned char *smem = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
   float *raw = reinterpret_cast<float *>(smem);            // [2][NARR][ARR]
   float *dX = raw + 2 * NARR * ARR;                        // [TY][DXP]
-  float *dY = dX + TY * DXP;                               // [DYH][TX]
-  float2 *su = reinterpret_cast<float2 *>(dY + DYH * TX);  // [TY][SUP] (offset is an even float count)
+  float2 *su = reinterpret_cast<float2 *>(dX + TY * DXP);  // [TY][SUP] (offset is an even float count)
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ TileInfo s_info[2];
   __shared__ TileInfo s_pinfo;  // thread 0's last prepared tile (per-instance scalars reused while it repeats)
@@ -273,6 +273,14 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
     s_pinfo.inst = -1;
     if ((int)blockIdx.x < ntiles) prepare(blockIdx.x, batch ? prm.tiles[blockIdx.x] : 0, 0);
   }
+  if (PREC == P_MIXED && prm.map_c < 0) {
+    // no delta array in this stage: the y sweep reads the delta slots all the same, so they hold zeros
+    // (no load ever writes them)
+    for (int i = tid; i < ARR; i += NT) {
+      raw[2 * ARR + i] = 0.0f;
+      raw[NARR * ARR + 2 * ARR + i] = 0.0f;
+    }
+  }
   __syncthreads();
 
   uint32_t phase = 0;  // bit b: parity of the next completion of bars[b]
@@ -323,7 +331,7 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
     const float *C = A + 2 * ARR;
     const bool has_delta = PREC == P_MIXED && prm.map_c >= 0;
 
-    // ---- 1. differences (rows by warp, columns by lane: no division, conflict-free); the
+    // ---- 1. x differences (rows by warp, columns by lane: no division, conflict-free); the
     // MIXED variant without a delta array (stage 1) is a separate loop, so that it reads two
     // arrays, not three
     auto diff_pass = [&](auto with_delta) {
@@ -343,13 +351,6 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
           dX[r * DXP + c] = cell_diff(i0, i0 + 1) * d.rdx;
         }
       }
-      for (int r = warp; r < DYH; r += NT / 32) {
-#pragma unroll
-        for (int c = lane; c < TX; c += 32) {
-          const int i0 = r * SW + c + 4;
-          dY[r * TX + c] = cell_diff(i0, i0 + SW) * d.rdy;
-        }
-      }
     };
     if (has_delta) diff_pass(std::true_type{});
     else diff_pass(std::false_type{});
@@ -366,8 +367,31 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
     float ym[K], yp[K];
     {
       const float *vx = dX + lane * DXP + K * warp;
-      const float *vy = dY + (K * segY) * TX + colY;
-      auto v_at = [&](int m) { return make_float2(vx[m], vy[m * TX]); };
+      // the y differences of the column segment, formed here from the tile arrays like the x
+      // differences of the differences pass; v_at is called for m = 0, 1, 2, ... in order, so each
+      // position loads one new row and reuses the previous one
+      const int iy = (K * segY) * SW + colY + 4;
+      float pa = A[iy], pb = 0.0f, pc = 0.0f;
+      if (PREC == P_MIXED) {
+        pb = B[iy];
+        pc = C[iy];
+      }
+      auto v_at = [&](int m) {
+        const int i1 = iy + (m + 1) * SW;
+        float dy;
+        if (PREC == P_MIXED) {
+          const float a1 = A[i1], b1 = B[i1], c1 = C[i1];
+          dy = (a1 - pa) + ((b1 - pb) + (c1 - pc));
+          pa = a1;
+          pb = b1;
+          pc = c1;
+        } else {
+          const float a1 = A[i1];
+          dy = a1 - pa;
+          pa = a1;
+        }
+        return make_float2(vx[m], dy * d.rdy);
+      };
       auto emit = [&](int q, float2 dm, float2 dp) {
         su[lane * SUP + K * warp + q] = make_float2(dm.x, dp.x);
         ym[q] = dm.y;
@@ -457,7 +481,7 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
     ++run_tiles;
     const bool more = next < ntiles;
     if (more && !s_info[buf ^ 1].skip && s_info[buf ^ 1].inst == i_inst) {
-      // no barrier: the next tile's differences pass writes only dX and dY, which this tile read
+      // no barrier: the next tile's differences pass writes only dX, which this tile read
       // before the barrier after the sweeps; su and raw[buf] are rewritten only after the next
       // tile's first barrier, which every thread reaches after finishing this tile
       continue;
@@ -512,7 +536,7 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
     amx = amy = 0.0f;
     bad = false;
     run_tiles = 0;
-    __syncthreads();  // raw[buf], dX, dY, su, s_info[buf] are free for the next tile
+    __syncthreads();  // raw[buf], dX, su, s_info[buf] are free for the next tile
   }
 }
 
