@@ -191,6 +191,15 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
       inst = e >> 16;
       tl = e & 0xffff;
     }
+    if (inst == s_info[b].inst) {
+      // the tile that last used this buffer belongs to the same instance (always so for a single
+      // grid): only the tile origin changes
+      TileInfo &bi = s_info[b];
+      bi.tx0 = (tl % bi.tiles_x) * TX;
+      bi.ty0 = (tl / bi.tiles_x) * TY;
+      if (!bi.skip) issue_loads(bi, b);
+      return;
+    }
     TileInfo info;
     if (inst == s_pinfo.inst) {
       info = s_pinfo;
@@ -271,6 +280,8 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
     mbar_init(&bars[1], 1);
     fence_mbar_init();
     s_pinfo.inst = -1;
+    s_info[0].inst = -1;
+    s_info[1].inst = -1;
     if ((int)blockIdx.x < ntiles) prepare(blockIdx.x, batch ? prm.tiles[blockIdx.x] : 0, 0);
   }
   if (PREC == P_MIXED && prm.map_c < 0) {
