@@ -355,12 +355,20 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
           return A[i1] - A[i0];
         }
       };
+      // the first TX cells of every row by whole warps, the last DXW - TX cells of all rows together
+      // (a third pass per row would keep only 5 of 32 lanes busy)
+      static_assert(TX % 32 == 0 && DXW - TX < 32, "x-difference row split");
       for (int r = warp; r < TY; r += NT / 32) {
 #pragma unroll
-        for (int c = lane; c < DXW; c += 32) {
+        for (int c = lane; c < TX; c += 32) {
           const int i0 = (r + 3) * SW + c + 1;
           dX[r * DXP + c] = cell_diff(i0, i0 + 1) * d.rdx;
         }
+      }
+      for (int j = tid; j < TY * (DXW - TX); j += NT) {
+        const int r = j / (DXW - TX), c = TX + j % (DXW - TX);
+        const int i0 = (r + 3) * SW + c + 1;
+        dX[r * DXP + c] = cell_diff(i0, i0 + 1) * d.rdx;
       }
     };
     if (has_delta) diff_pass(std::true_type{});
