@@ -101,7 +101,12 @@ enum { ALW_DT_CFL = 0, ALW_DT_DX53 = 1 };
  * MIXED: stencil arithmetic in float; phi^n is held as an unevaluated sum of
  * two floats (hi + lo, about 48 significant bits) and the RK stages store
  * float increments phi_s - phi^n, so the accumulation of phi over long runs
- * keeps double-class precision; the CFL reduction is in double. */
+ * keeps double-class precision; the CFL reduction is in double.  In FP32 and
+ * MIXED the square roots, logarithms, reciprocals, sines and cosines of the
+ * stencil and of the Hamiltonians are the GPU's hardware approximations
+ * (relative error of a few units in the last float place; the logarithm's
+ * absolute error is about 2^-22), so float results match the FP64 oracle to
+ * float accuracy, not bit for bit. */
 enum { ALW_PREC_FP64 = 0, ALW_PREC_FP32 = 1, ALW_PREC_MIXED = 2 };
 
 typedef struct {
