@@ -210,6 +210,16 @@ def _stream_handle(stream) -> int:
 
 # ---------------------------------------------------------------- solver
 
+def _host_out(out, shape) -> np.ndarray:
+    """A new float64 array of `shape`, or the caller's array after checking that it can take the result."""
+    if out is None:
+        return np.empty(shape, dtype=np.float64)
+    if not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous
+            and out.flags.writeable and out.shape == tuple(shape)):
+        raise ValueError(f"out must be a writeable C-contiguous float64 array of shape {tuple(shape)}")
+    return out
+
+
 class Solver:
     """One HJ problem on the GPU (alw_create ... alw_destroy)."""
 
@@ -276,8 +286,9 @@ class Solver:
     def sync(self):
         check(self._L.alw_sync(self._h))
 
-    def get_phi(self) -> np.ndarray:
-        out = np.empty(self.shape, dtype=np.float64)
+    def get_phi(self, out=None) -> np.ndarray:
+        """phi on the host; into `out` (a C-contiguous float64 array of the grid's shape) when given."""
+        out = _host_out(out, self.shape)
         check(self._L.alw_get_phi(self._h, out.ctypes.data, out.size))
         return out
 
@@ -374,8 +385,9 @@ class Batch:
         check(self._L.alw_batch_run(self._h, ctypes.byref(r)))
         return r.value
 
-    def get_phi(self, i: int) -> np.ndarray:
-        out = np.empty(self.shapes[i], dtype=np.float64)
+    def get_phi(self, i: int, out=None) -> np.ndarray:
+        """phi of instance i on the host; into `out` (C-contiguous float64, the instance's shape) when given."""
+        out = _host_out(out, self.shapes[i])
         check(self._L.alw_batch_get_phi(self._h, int(i), out.ctypes.data, out.size))
         return out
 

@@ -4,6 +4,7 @@ device instead of falling back to the CPU."""
 import ctypes
 import os
 
+import numpy as np
 import pytest
 
 from paper_1909_13263_gb300 import build, native
@@ -41,3 +42,17 @@ def test_library_is_built_for_sm_103a(lib):
     # the build passes exactly one -gencode for compute_103a / sm_103a
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
     assert os.path.getsize(native.LIB_PATH) > 0
+
+
+def test_result_buffer_argument_is_checked():
+    # get_phi(out=...) writes into the caller's array only when it can take the result unchanged
+    a = np.zeros((3, 4))
+    assert native._host_out(a, (3, 4)) is a
+    assert native._host_out(None, (3, 4)).shape == (3, 4)
+    for bad in (np.zeros((4, 3)), np.zeros((3, 4), dtype=np.float32), np.zeros((4, 3)).T, [[0.0] * 4] * 3):
+        with pytest.raises(ValueError):
+            native._host_out(bad, (3, 4))
+    ro = np.zeros((3, 4))
+    ro.flags.writeable = False
+    with pytest.raises(ValueError):
+        native._host_out(ro, (3, 4))

@@ -45,6 +45,29 @@ def test_checkpoint_resume_reproduces_uninterrupted_run(precision):
         assert np.array_equal(resumed, full)
 
 
+def test_results_into_caller_buffers_equal_returned_results():
+    case = Case(2, 96, 80, "burgers2d", precision="mixed", lo=-2.0, hi=2.0)
+    phi0 = case.field(seed=5, kind="smooth")
+    with case.solver() as s:
+        s.set_phi0(phi0)
+        s.step_to(0.01)
+        own = s.get_phi()
+        buf = np.full(own.shape, np.nan)
+        assert s.get_phi(out=buf) is buf
+        assert np.array_equal(buf, own)
+    kw = dict(xlo=-2.0, xhi=2.0, ylo=-2.0, yhi=2.0)
+    with native.Batch(precision="mixed") as b:
+        b.add(nx=96, ny=80, ham="burgers2d", phi0=phi0, t_final=0.01, **kw)
+        b.add(nx=64, ny=64, ham="negcos2d", phi0=phi0[:64, :64].copy(), t_final=0.005, **kw)
+        b.run()
+        for k, shape in enumerate([(80, 96), (64, 64)]):
+            buf = np.full(shape, np.nan)
+            assert b.get_phi(k, out=buf) is buf
+            assert np.array_equal(buf, b.get_phi(k))
+        with pytest.raises(ValueError):
+            b.get_phi(0, out=np.zeros((96, 80)))
+
+
 def test_invalid_arguments_are_rejected():
     with pytest.raises(native.AlwError) as e:
         native.Solver(dim=2, nx=16, ny=16, xlo=0, xhi=1, ylo=0, yhi=1, ham="burgers1d")
