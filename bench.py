@@ -187,6 +187,27 @@ def _oracle_sample(n: int, steps: int):
     return t0, time.monotonic(), st
 
 
+def _oracle_case(kind: str, n: int, steps: int):
+    """One timed oracle run of about `steps` RK3 steps with the CFL time step: (start, end, steps, nodes).
+
+    kind "ex3": Example 3 on an n x n grid (as _oracle_sample); "k1": 1D, [-1, 1) periodic with n nodes,
+    phi0 = -cos(pi x), H = (p + 1)^2 / 2 (the 1D accuracy workload), local lagged alpha."""
+    if kind == "ex3":
+        t0, t1, st = _oracle_sample(n, steps)
+        return t0, t1, st, n * n
+    import oracle
+    from paper_1909_13263_gb300 import inputs
+
+    x, dx = inputs.axis(n, -1.0, 1.0, "periodic")
+    phi0 = inputs.phi0_negcos_1d(x)
+    cfg = oracle.make_cfg(dim=1, nx=n, dx=dx, ham="burgers1d", weights="arclength", alpha_mode="local_lagged")
+    a, _ = oracle.alpha_of(cfg, phi0)
+    dt = 0.6 * dx / a[0]
+    t0 = time.monotonic()
+    _, st, _, _, _ = oracle.solve(cfg, phi0, steps * dt * 0.999999, alpha_state=a.copy())
+    return t0, time.monotonic(), st, n
+
+
 def _host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -216,10 +237,14 @@ class OraclePool:
 
     def rate(self, n: int, steps: int):
         """Aggregate point-updates/s, the span in seconds and the steps per instance for one sample."""
-        res = self._pool.starmap(_oracle_sample, [(n, steps)] * self.workers, chunksize=1)
-        span = max(t1 for _, t1, _ in res) - min(t0 for t0, _, _ in res)
-        st = res[0][2]
-        return self.workers * n * n * st / span, span, st
+        return self.rate_case("ex3", n, steps)
+
+    def rate_case(self, kind: str, n: int, steps: int):
+        """As rate, for any workload of _oracle_case."""
+        res = self._pool.starmap(_oracle_case, [(kind, n, steps)] * self.workers, chunksize=1)
+        span = max(r[1] for r in res) - min(r[0] for r in res)
+        st, nodes = res[0][2], res[0][3]
+        return self.workers * nodes * st / span, span, st
 
     def close(self):
         self._pool.close()
@@ -354,6 +379,57 @@ def bench_serving(args, stream, rate):
             "p99_speedup_vs_serial": serial["p99_s"] / served["p99_s"],
             "solves_per_s_vs_serial": served["solves_per_s"] / serial["solves_per_s"],
             "budget_gb": args.serve_budget_gb}
+
+
+def _host_description() -> dict:
+    import platform
+
+    d = {"machine": platform.machine(), "cores": _host_cores(), "cpu_count": os.cpu_count()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:") or line.startswith("Vendor ID:"):
+                k, v = line.split(":", 1)
+                d[k.strip().lower().replace(" ", "_")] = v.strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return d
+
+
+def run_oracle_report(args):
+    """The FP64 CPU oracle timed on the host cores (one JSON line): one core, and every core at once with
+    one independent instance per core, for the 1D accuracy workload at N = 40, 80, 160, 320 and for
+    Example 3 on 400^2 and 2048^2; 8192^2 extrapolated from the 2048^2 cost per node and step.  Each
+    sample is sized for about half a second of one-core work (at least one step)."""
+    import oracle
+
+    oracle.build()
+    cores = args.cpu_cores or _host_cores()
+    pool = OraclePool(cores)
+    out = {"report": "oracle", "unit": "point-updates/s", "host": _host_description(), "workers": cores}
+    # per-node-step cost guesses (s) that size the samples; the measured cost replaces them
+    guess = {"k1": 6e-7, "ex3": 1.6e-6}
+    for kind, sizes, name in (("k1", (40, 80, 160, 320), "k1_burgers1d"), ("ex3", (400, 2048), "ex3_burgers2d")):
+        rows = {}
+        for n in sizes:
+            nodes = n if kind == "k1" else n * n
+            steps = max(1, int(0.5 / (guess[kind] * nodes)))
+            t0, t1, st, _ = _oracle_case(kind, n, steps)
+            one = nodes * st / (t1 - t0)
+            allc, span, st2 = pool.rate_case(kind, n, steps)
+            rows[f"{n}" if kind == "k1" else f"{n}sq"] = {
+                "steps": st, "ms_per_step_one_core": 1e3 * (t1 - t0) / st, "one_core": one,
+                "all_cores": allc, "all_cores_span_s": span}
+        out[name] = rows
+    big = out["ex3_burgers2d"]["2048sq"]
+    n8 = 8192 * 8192
+    out["ex3_burgers2d"]["8192sq_extrapolated"] = {
+        "ms_per_step_one_core": 1e3 * n8 / big["one_core"], "one_core": big["one_core"],
+        "all_cores": big["all_cores"], "ms_per_step_all_cores": 1e3 * n8 / big["all_cores"],
+        "from": "2048^2 cost per node and step"}
+    pool.close()
+    print(json.dumps(out), flush=True)
+    return 0
 
 
 def run_sizes_report(args):
@@ -679,8 +755,9 @@ def main():
     ap.add_argument("--serve-round-tiles", type=int, default=None,
                     help="tile limit of a server round (default: the server's own, four kernel waves; 0: none)")
     ap.add_argument("--serve-rates", type=str, default="", help="comma-separated arrival rates (a sweep)")
-    ap.add_argument("--report", choices=["", "precision", "sizes"], default="",
-                    help="precision: errors of the float paths against FP64 and the exact solution")
+    ap.add_argument("--report", choices=["", "precision", "sizes", "oracle"], default="",
+                    help="precision: errors of the float paths against FP64 and the exact solution; sizes: "
+                         "device throughput by grid size; oracle: the FP64 CPU oracle timed on the host cores")
     ap.add_argument("--report-ex3-sizes", type=str, default="400,2048",
                     help="precision report: grid sides of Example 3 (comma-separated)")
     ap.add_argument("--report-ex10-sizes", type=str, default="1024",
@@ -696,6 +773,8 @@ def main():
         return run_precision_report(args)
     if args.report == "sizes":
         return run_sizes_report(args)
+    if args.report == "oracle":
+        return run_oracle_report(args)
     return run_ours(args)
 
 
