@@ -372,3 +372,24 @@ def test_nonconvex_alpha_is_the_interval_maximum():
     for kind, hp in (("burgers1d", lambda p: abs(p + 1)), ("advect1d", lambda p: 1.0)):
         um, up = -0.7, 1.3
         assert oracle.node_alpha(kind, 1, um, up)[0] == pytest.approx(max(hp(um), hp(up)))
+
+
+@pytest.mark.parametrize("dim,ham,bc,alpha", [(2, "burgers2d", "periodic", "global_lagged"),
+                                              (2, "optctrl2d", "linextrap", "local_lagged"),
+                                              (2, "sin2d", "linextrap", "fixed"),
+                                              (1, "nonconvex1d", "periodic", "local_lagged")])
+def test_single_node_L_matches_the_grid_L(dim, ham, bc, alpha):
+    # the one-node operator (used to check sampled nodes of very large grids) is the grid operator
+    # L = -H-hat of Eq. LF at that node, boundaries and node coordinates included
+    rng = np.random.default_rng(11)
+    nx, ny = (23, 17) if dim == 2 else (29, 1)
+    phi = rng.standard_normal((ny, nx) if dim == 2 else nx)
+    cfg = oracle.make_cfg(dim=dim, nx=nx, ny=ny, bc=bc, dx=0.13, dy=0.11, ham=ham, alpha_mode=alpha,
+                          alpha_fixed=(1.0, 1.5), xlo=-1.3, ylo=0.4)
+    a = np.array([1.7, 2.3])
+    full = oracle.L_of(cfg, phi, a)
+    for j in range(ny):
+        for i in range(nx):
+            one = oracle.point_L(cfg, phi, i, j, a)
+            ref = full[j, i] if dim == 2 else full[i]
+            assert one == pytest.approx(ref, rel=1e-14, abs=1e-14), (i, j)
