@@ -112,6 +112,8 @@ def test_fp64_solve_matches_oracle(case):
     Case(1, 300, 1, "burgers1d", alpha_mode="local_lagged"),
     Case(2, 130, 70, "optctrl2d", lo=-math.pi, hi=math.pi),
     Case(2, 70, 66, "optctrl2d", lo=-math.pi, hi=math.pi, alpha_mode="local_lagged"),
+    Case(2, 97, 45, "eikonal2d", lo=0.0, hi=1.0),
+    Case(2, 70, 66, "eikonal2d", bc="linextrap", alpha_mode="local_lagged"),
 ], ids=_ids)
 def test_float_rk_stages_within_bound(case, weights, precision):
     case.weights, case.precision = weights, precision
@@ -126,6 +128,36 @@ def test_float_rk_stages_within_bound(case, weights, precision):
             got = s.get_stage_phi(stage) if stage < 3 else s.get_phi()
             errs.append(rel_err(got, ref[stage - 1]))
     assert max(errs) <= F32_STAGE_TOL, errs
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed"])
+@pytest.mark.parametrize("weights", ["arclength", "jp"])
+@pytest.mark.parametrize("kind", ["constant", "linear"])
+def test_degenerate_data_stages_match_oracle(kind, weights, precision):
+    # constant data (every difference zero: the vanishing-interval branch of the arc-length means and
+    # zero Jiang-Peng indicators) and linear data (every second difference zero), where each stage
+    # is phi + dt L with L = -H(a, b) at every node
+    nx, ny = 70, 37
+    if kind == "constant":
+        case = Case(2, nx, ny, "negcos2d", weights=weights, precision=precision)
+        phi0 = np.full((ny, nx), 0.7)
+    else:
+        case = Case(2, nx, ny, "burgers2d", bc="linextrap", weights=weights, precision=precision)
+        x, _ = inputs.axis(nx, -1.0, 1.0, "linextrap")
+        y, _ = inputs.axis(ny, -1.0, 1.0, "linextrap")
+        X, Y = np.meshgrid(x, y, indexing="xy")
+        phi0 = 0.3 * X - 0.45 * Y + 0.2
+    dt = _stage_dt(case, phi0)
+    ref = oracle_stages(case, phi0, dt)
+    tol = FP64_TOL if precision == "fp64" else F32_STAGE_TOL
+    with case.solver() as s:
+        s.set_phi0(phi0)
+        errs = []
+        for stage in (1, 2, 3):
+            s.run_stage(stage, dt)
+            got = s.get_stage_phi(stage) if stage < 3 else s.get_phi()
+            errs.append(rel_err(got, ref[stage - 1]))
+    assert max(errs) <= tol, errs
 
 
 def test_mixed_keeps_double_class_phi_between_steps():
