@@ -393,3 +393,57 @@ def test_single_node_L_matches_the_grid_L(dim, ham, bc, alpha):
             one = oracle.point_L(cfg, phi, i, j, a)
             ref = full[j, i] if dim == 2 else full[i]
             assert one == pytest.approx(ref, rel=1e-14, abs=1e-14), (i, j)
+
+
+def test_solve_rk3_translates_cubic_data_exactly():
+    # Step 5 as orc_solve runs it: phi_t + phi_x = 0 (H = p, Example 1's equation) with cubic data on a
+    # linear-extrapolation grid.  Every candidate of Step 2 is exact for cubics, so at nodes whose
+    # stencils never reach a ghost, L = -phi_x exactly for any weights and the LF term vanishes
+    # (u^+ = u^-).  One Shu-Osher step then gives phi - dt phi' + dt^2 phi''/2 - dt^3 phi'''/6,
+    # the cubic translated by dt: each stage's dependence widens by three nodes, so nodes 9..n-10
+    # must equal p(x - dt).  A wrong stage weight (3/4, 1/4, 1/3, 2/3) breaks this.
+    rng = np.random.default_rng(1909)
+    n, lo, hi = 41, -1.0, 1.0
+    dx = (hi - lo) / (n - 1)
+    x = lo + dx * np.arange(n)
+    for _ in range(3):
+        c = rng.normal(size=4)
+        p = lambda z: c[0] + c[1] * z + c[2] * z**2 + c[3] * z**3
+        cfg = oracle.make_cfg(dim=1, nx=n, dx=dx, ham="advect1d", bc="linextrap", alpha_mode="fixed",
+                              alpha_fixed=(1.0, 0.0), xlo=lo)
+        dt = 0.37 * dx      # below the CFL step 0.6 dx: one (clipped) step
+        phi, steps, t, _, st = oracle.solve(cfg, p(x), dt)
+        assert st == 0 and steps == 1 and t == dt
+        np.testing.assert_allclose(phi[9:n - 9], p(x[9:n - 9] - dt), rtol=0, atol=1e-13)
+        # the boundary nodes use linearly extrapolated ghosts, which are not exact for cubics
+        assert np.abs(phi[:3] - p(x[:3] - dt)).max() > 1e-9
+
+
+@pytest.mark.parametrize("weights", ["arclength", "jp"])
+def test_linextrap_ghosts_exact_on_linear_data(weights):
+    # The ghost values phi_{-m} = (1+m) phi_0 - m phi_1 (and the mirror image at the right end) extend
+    # linear data exactly, so every one-sided derivative -- also at the three nodes next to each end,
+    # whose stencils reach the ghosts -- equals the slope.  A wrong sign or index in a ghost fails here.
+    rng = np.random.default_rng(7)
+    n = 13
+    dx = 0.25
+    x = dx * np.arange(n)
+    b = -0.4 - rng.random()    # slopes of order one: rounding of the data stays far below 1e-13
+    cfg = oracle.make_cfg(dim=1, nx=n, dx=dx, ham="advect1d", bc="linextrap", weights=weights)
+    um, up, _, _ = oracle.derivs(cfg, 0.3 + b * x)
+    np.testing.assert_allclose(um, b, rtol=1e-13, atol=0)
+    np.testing.assert_allclose(up, b, rtol=1e-13, atol=0)
+    # 2D: slopes in both directions, ragged sizes
+    ny, nx, dy = 9, 11, 0.2
+    bx, by = 0.5 + rng.random(2)
+    X, Y = np.meshgrid(dx * np.arange(nx), dy * np.arange(ny))
+    cfg2 = oracle.make_cfg(dim=2, nx=nx, ny=ny, dx=dx, dy=dy, ham="burgers2d", bc="linextrap", weights=weights)
+    um, up, vm, vp = oracle.derivs(cfg2, -1.1 + bx * X + by * Y)
+    for a in (um, up):
+        np.testing.assert_allclose(a, bx, rtol=1e-13, atol=0)
+    for a in (vm, vp):
+        np.testing.assert_allclose(a, by, rtol=1e-13, atol=0)
+    # quadratic data is not extended exactly: the boundary derivatives differ from the exact ones
+    q = 0.5 * x**2
+    um, up, _, _ = oracle.derivs(cfg, q)
+    assert abs(um[0] - 0.0) > 1e-3 and np.allclose(um[4:-4], x[4:-4], rtol=1e-12, atol=1e-12)
