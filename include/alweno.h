@@ -141,9 +141,11 @@ typedef struct {
 
 typedef struct alw_solver alw_solver;
 
-/* Device allocator hook (process-wide).  alloc returns device memory of at
- * least `bytes` usable in stream order on `stream`, or NULL; free releases it.
- * Pass NULL to restore the default (cudaMallocAsync/cudaFreeAsync). */
+/* Device allocator hook (process-wide; no counterpart in the paper).  alloc
+ * returns device memory of at least `bytes` usable in stream order on
+ * `stream`, or NULL; free releases it.  Pass NULL to restore the default
+ * (cudaMallocAsync/cudaFreeAsync: the C library depends on no framework; the
+ * Python binding installs the PyTorch caching allocator through this hook). */
 typedef struct {
   void *(*alloc)(size_t bytes, void *stream, void *ctx);
   void (*free)(void *ptr, size_t bytes, void *stream, void *ctx);
@@ -151,7 +153,8 @@ typedef struct {
 } alw_allocator;
 alw_status alw_set_allocator(const alw_allocator *allocator);
 
-/* Library version string and the thread-local message of the last error. */
+/* Library version string and the thread-local message of the last error (no
+ * counterpart in the paper). */
 const char *alw_version(void);
 const char *alw_last_error(void);
 
@@ -162,14 +165,18 @@ const char *alw_last_error(void);
  * reverse), ALW_ENOMEM, ALW_ECUDA. */
 alw_status alw_create(const alw_grid *grid, const alw_hamiltonian *ham, const alw_scheme *scheme,
                       void *cuda_stream, alw_solver **out);
+/* Release the solver and its device memory (no counterpart in the paper); NULL is ALW_EINVAL. */
 alw_status alw_destroy(alw_solver *s);
 
-/* Set phi(., 0) from a host array of n = nx*ny doubles (copied); resets t to
- * 0, the step count and the lagged alpha.  ALW_EINVAL if n != nx*ny. */
+/* Set the initial data phi(x, 0) = phi^0(x) of Eq. HJ from a host array of
+ * n = nx*ny doubles (copied); resets t to 0, the step count and the lagged
+ * alpha (a prime pass over phi^0 supplies the first, Step 5 with the LF flux).
+ * ALW_EINVAL if n != nx*ny. */
 alw_status alw_set_phi0(alw_solver *s, const double *host_phi, size_t n);
 
-/* Same from a device array (e.g. a torch tensor's data pointer) of n values of
- * `dtype` (0 = double, 1 = float), contiguous row-major; copied on the stream. */
+/* Same (initial data of Eq. HJ) from a device array (e.g. a torch tensor's data
+ * pointer) of n values of `dtype` (0 = double, 1 = float), contiguous
+ * row-major; copied on the stream.  ALW_EINVAL for another dtype or n. */
 alw_status alw_set_phi0_device(alw_solver *s, const void *dev_phi, int32_t dtype, size_t n);
 
 /* Advance to t_final with TVD-RK3 (Step 5): whole steps, the last one clipped.
@@ -179,8 +186,9 @@ alw_status alw_set_phi0_device(alw_solver *s, const void *dev_phi, int32_t dtype
  * non-finite (phi is left at the step where it was detected). */
 alw_status alw_step_to(alw_solver *s, double t_final, int64_t *steps_out);
 
-/* Advance exactly nsteps RK3 steps with the CFL time step (no clipping; used
- * for throughput measurement).  Asynchronous: returns after enqueueing. */
+/* Advance exactly nsteps TVD-RK3 steps (Step 5) with the CFL time step of
+ * Sec. 3 (no clipping; used for throughput measurement).  Asynchronous:
+ * returns after enqueueing. */
 alw_status alw_advance(alw_solver *s, int64_t nsteps);
 
 /* Enqueue a single RK stage (1, 2 or 3) with the given dt (asynchronous; for
@@ -190,11 +198,15 @@ alw_status alw_advance(alw_solver *s, int64_t nsteps);
  * non-finite dt. */
 alw_status alw_run_stage(alw_solver *s, int32_t stage, double dt);
 
-/* Wait for the solver's stream; returns ALW_ENONFINITE if flagged. */
+/* Wait for the solver's stream (no counterpart in the paper); returns
+ * ALW_ENONFINITE if a stage flagged a non-finite dH/dp. */
 alw_status alw_sync(alw_solver *s);
 
-/* Copy phi (interior, n = nx*ny doubles) to a caller-owned host buffer.
- * For MIXED the two float parts are summed exactly in double. */
+/* Copy the solution phi(x, t) of Eq. HJ at the solver's current time
+ * (interior, n = nx*ny doubles) to a caller-owned host buffer; for MIXED the
+ * two float parts are summed exactly in double.  alw_get_phi_device writes n
+ * values of `dtype` (0 = double, 1 = float) to a caller-owned device array.
+ * ALW_EINVAL if n != nx*ny. */
 alw_status alw_get_phi(alw_solver *s, double *host_out, size_t n);
 alw_status alw_get_phi_device(alw_solver *s, void *dev_out, int32_t dtype, size_t n);
 
@@ -202,12 +214,13 @@ alw_status alw_get_phi_device(alw_solver *s, void *dev_out, int32_t dtype, size_
  * phi_2 in the notation of Step 5), as doubles. */
 alw_status alw_get_stage_phi(alw_solver *s, int32_t stage, double *host_out, size_t n);
 
-/* Time, steps, lagged alpha; and restoring them with phi (checkpoint/resume:
- * resuming reproduces an uninterrupted run bit for bit). */
+/* Time, steps, lagged alpha; and restoring them with phi (checkpoint/resume,
+ * no counterpart in the paper: resuming reproduces an uninterrupted run bit
+ * for bit, to a tie in the hi/lo split of MIXED). */
 alw_status alw_get_state(alw_solver *s, alw_state *state);
 alw_status alw_set_state(alw_solver *s, const alw_state *state, const double *host_phi, size_t n);
 
-/* Device bytes held by the solver. */
+/* Device bytes held by the solver (no counterpart in the paper). */
 alw_status alw_memory_bytes(alw_solver *s, size_t *bytes);
 
 /* ------------------------------------------------------------------------
@@ -235,6 +248,9 @@ typedef struct {
                                folds that instance's alpha) less often while neighbouring blocks
                                still run together; 0 = one contiguous stretch per CTA.  The
                                autotuner uses 4. */
+  int32_t tile_w;           /* tile width in nodes: 64 (tiles 64 x 32) or 32 (tiles 32 x 32: twice the
+                               tiles, each with 1.1x the halo reads per node); 0 = 64.  The
+                               autotuner times both on the batch's own work list. */
 } alw_batch_tuning;
 
 alw_status alw_batch_create(const alw_scheme *scheme, void *cuda_stream, alw_batch **out);
@@ -243,7 +259,8 @@ alw_status alw_batch_create(const alw_scheme *scheme, void *cuda_stream, alw_bat
  * receives its index.  ALW_EBUSY after the batch has been built or run. */
 alw_status alw_batch_add(alw_batch *b, const alw_grid *grid, const alw_hamiltonian *ham, const double *host_phi0,
                          size_t n, double t_final, int32_t *id_out);
-/* Fix the tuning (NULL: let the autotuner choose on the next run). */
+/* Fix the tuning (NULL: let the autotuner choose on the next run).  ALW_EINVAL
+ * for a field outside its range (tile_w other than 0, 32, 64). */
 alw_status alw_batch_set_tuning(alw_batch *b, const alw_batch_tuning *tuning);
 alw_status alw_batch_get_tuning(alw_batch *b, alw_batch_tuning *tuning);
 /* Lay out the device arena, upload every instance and tune the work list now
@@ -254,6 +271,9 @@ alw_status alw_batch_build(alw_batch *b);
  * replays_out (nullable): graph replays used.  ALW_ENONFINITE if an instance
  * saw a non-finite dH/dp (the others still finish). */
 alw_status alw_batch_run(alw_batch *b, int64_t *replays_out);
+/* Instance id's phi at its current time (n = its nx*ny doubles, caller-owned host
+ * buffer) and its state; ALW_ENOTFOUND for an unknown id, ALW_EINVAL before
+ * the first run or for a wrong n.  Device bytes held; release everything. */
 alw_status alw_batch_get_phi(alw_batch *b, int32_t id, double *host_out, size_t n);
 alw_status alw_batch_get_state(alw_batch *b, int32_t id, alw_state *state);
 alw_status alw_batch_memory_bytes(alw_batch *b, size_t *bytes);
@@ -307,6 +327,7 @@ alw_status alw_server_submit(alw_server *s, const alw_grid *grid, const alw_hami
  * result is copied and the request is forgotten. */
 alw_status alw_server_poll(alw_server *s, uint64_t req_id, double timeout_s, int32_t *done, double *host_out,
                            size_t n, alw_request_info *info);
+/* Counters of the server (submitted, admitted, completed, queued, rounds, arena rows). */
 alw_status alw_server_stats_get(alw_server *s, alw_server_stats *stats);
 /* Stops the worker after its current round and frees everything. */
 alw_status alw_server_destroy(alw_server *s);
@@ -327,7 +348,11 @@ alw_status alw_server_destroy(alw_server *s);
  * allocated or freed.
  *
  * The first call on a device looks up the array's address and should be made
- * before any stream capture.  Every call clears the storage it uses; calls
+ * before any stream capture.  CUDA loads device code lazily by default, so
+ * that first call also loads this library's device code on the device and
+ * reserves the 16 MiB there (or fails with ALW_ECUDA if the device has no
+ * room left): make it before a pool takes the device's memory or a real-time
+ * phase begins, and check its status.  Every call clears the storage it uses; calls
  * whose GPU work overlaps (e.g. on two streams at once) race on the shared
  * storage and must be serialised by the caller.  Work is enqueued on
  * cuda_stream and the call returns after it completes; ALW_ENONFINITE if

@@ -5,12 +5,16 @@
 // common pitch, so one set of TMA tensor maps serves all of them; each
 // instance keeps its own device-side time, dt and alpha state.
 //
-// A small autotuner picks, per batch shape, the work-list order (and with it
-// how neighbouring tiles share L2 and how the tail of the largest instances
-// lines up) by timing reduction-only passes over the whole work list -- the
-// full derivative work of a stage without any store, so the state of the
-// batch is untouched -- and chooses the number of RK steps per graph replay
-// from the amount of work per step.  Results are cached per batch shape.
+// A small autotuner picks, per batch shape, the tile width (64 x 32 or 32 x 32
+// tiles: the narrow ones halve the work of the smallest instances' tiles and
+// double the tiles in flight, at 1.1x the halo reads per node) and the
+// work-list order (and with it how neighbouring tiles share L2 and how the
+// tail of the largest instances lines up) by timing reduction-only passes over
+// the whole work list -- the full derivative work of a stage without any
+// store, so the state of the batch is untouched -- and chooses the number of
+// RK steps per graph replay from the amount of work per step.  Results are
+// cached per batch shape.  The arena is laid out for 64-wide tiles, which
+// covers the narrow ones, so both widths run on the same arrays.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -94,9 +98,11 @@ struct alw_batch {
   size_t arr_bytes = 0;
   void *H[2] = {nullptr, nullptr}, *Lo[2] = {nullptr, nullptr}, *D1 = nullptr, *D2 = nullptr;  // MIXED
   void *P = nullptr, *A = nullptr, *B = nullptr;                                               // FP32
-  CUtensorMap maps[6];
-  std::vector<InstDesc> h_inst;
-  InstDesc *d_inst = nullptr;
+  CUtensorMap maps[6];            // boxes of 64-wide tiles
+  CUtensorMap maps_narrow[6];     // boxes of 32-wide tiles
+  std::vector<InstDesc> h_inst;   // instance table for 64-wide tiles
+  std::vector<InstDesc> h_inst_narrow;  // the same with the tile counts of 32-wide tiles
+  InstDesc *d_inst = nullptr, *d_inst_narrow = nullptr;
   DevState *d_state = nullptr;
   DevState *h_state = nullptr;  // pinned mirror
   int *d_done = nullptr;
@@ -135,14 +141,21 @@ void free_pending(alw_batch *b) {
     }
 }
 
+bool narrow(const alw_batch *b) { return b->tuning.tile_w == kTile2DXNarrow; }
+
+// The instance table of the tuning's tile width.
+const std::vector<InstDesc> &insts(const alw_batch *b) { return narrow(b) ? b->h_inst_narrow : b->h_inst; }
+
 int cap_for(const alw_batch *b) {
-  return b->prec == P_MIXED ? stage2d_grid_cap_mixed(b->scheme.weights) : stage2d_grid_cap_f32(b->scheme.weights);
+  const int w = narrow(b) ? kTile2DXNarrow : kTile2DX;
+  return b->prec == P_MIXED ? stage2d_grid_cap_mixed(b->scheme.weights, w) : stage2d_grid_cap_f32(b->scheme.weights, w);
 }
 
 Stage2DParams batch_params(const alw_batch *b, int stage, int loop_mode, int ntiles) {
   Stage2DParams q;
   memset(&q, 0, sizeof q);
-  memcpy(q.maps, b->maps, sizeof q.maps);
+  memcpy(q.maps, narrow(b) ? b->maps_narrow : b->maps, sizeof q.maps);
+  q.tile_w = narrow(b) ? kTile2DXNarrow : kTile2DX;
   StageParams &p = q.p;
   p.pitch = b->pitch;
   p.dim = 2;
@@ -184,7 +197,7 @@ Stage2DParams batch_params(const alw_batch *b, int stage, int loop_mode, int nti
   }
   q.ntiles = ntiles;
   q.grid_ctas = b->tuning.grid_ctas;
-  q.insts = b->d_inst;
+  q.insts = narrow(b) ? b->d_inst_narrow : b->d_inst;
   q.states = b->d_state;
   q.tiles = b->d_tiles;
   q.done_count = b->d_done;
@@ -197,22 +210,22 @@ int launch(const alw_batch *b, const Stage2DParams &q) {
 
 // Work list of the instances for which `live[i]` holds, in the requested order.
 std::vector<int> ordered_list(const alw_batch *b, const std::vector<char> &live, int order) {
+  const std::vector<InstDesc> &I = insts(b);
   std::vector<int> ids;
-  for (size_t i = 0; i < b->h_inst.size(); ++i)
+  for (size_t i = 0; i < I.size(); ++i)
     if (live[i]) ids.push_back((int)i);
   if (order == ALW_ORDER_LARGEST_FIRST)
-    std::stable_sort(ids.begin(), ids.end(),
-                     [&](int x, int y) { return b->h_inst[x].ntiles > b->h_inst[y].ntiles; });
+    std::stable_sort(ids.begin(), ids.end(), [&](int x, int y) { return I[x].ntiles > I[y].ntiles; });
   std::vector<int> list;
   if (order == ALW_ORDER_INTERLEAVED) {
     int maxt = 0;
-    for (int i : ids) maxt = std::max(maxt, b->h_inst[i].ntiles);
+    for (int i : ids) maxt = std::max(maxt, I[i].ntiles);
     for (int t = 0; t < maxt; ++t)
       for (int i : ids)
-        if (t < b->h_inst[i].ntiles) list.push_back(i * 65536 + t);
+        if (t < I[i].ntiles) list.push_back(i * 65536 + t);
   } else {
     for (int i : ids)
-      for (int t = 0; t < b->h_inst[i].ntiles; ++t) list.push_back(i * 65536 + t);
+      for (int t = 0; t < I[i].ntiles; ++t) list.push_back(i * 65536 + t);
   }
   return list;
 }
@@ -330,8 +343,20 @@ alw_status build(alw_batch *b) {
     d.ly = b->scheme.dt_mode == ALW_DT_DX53 ? std::pow(dy, 5.0 / 3.0) : dy;
     pitch = std::max(pitch, d.tiles_x * kTile2DX + 2 * GX);
     rows += (long long)d.tiles_y * kTile2DY + 2 * GY;
-    total_tiles += d.ntiles;
   }
+  // the same instances cut into 32-wide tiles (inside the same padded rows: ceil(nx / 32) * 32
+  // never exceeds ceil(nx / 64) * 64)
+  b->h_inst_narrow = b->h_inst;
+  long long total_narrow = 0;
+  for (int i = 0; i < n; ++i) {
+    InstDesc &d = b->h_inst_narrow[i];
+    d.tiles_x = (d.nx + kTile2DXNarrow - 1) / kTile2DXNarrow;
+    d.ntiles = d.tiles_x * d.tiles_y;
+    total_tiles += b->h_inst[i].ntiles;
+    total_narrow += d.ntiles;
+    if (d.ntiles > 65535) return berr(ALW_EINVAL, "instance %d has more than 65535 tiles", i);
+  }
+  total_tiles = std::max(total_tiles, total_narrow);
   if (rows > (1ll << 31)) return berr(ALW_EINVAL, "batch too tall");
   b->pitch = pitch;
   b->rows = rows;
@@ -346,10 +371,12 @@ alw_status build(alw_batch *b) {
   }
   b->d_state = (DevState *)b->alloc(sizeof(DevState) * n);
   b->d_inst = (InstDesc *)b->alloc(sizeof(InstDesc) * n);
+  b->d_inst_narrow = (InstDesc *)b->alloc(sizeof(InstDesc) * n);
   b->d_done = (int *)b->alloc(sizeof(int));
   b->ntiles_alloc = (int)total_tiles;
   b->d_tiles = (int *)b->alloc(sizeof(int) * std::max<long long>(1, total_tiles));
-  if (!b->d_state || !b->d_inst || !b->d_done || !b->d_tiles) return berr(ALW_ENOMEM, "device allocation failed");
+  if (!b->d_state || !b->d_inst || !b->d_inst_narrow || !b->d_done || !b->d_tiles)
+    return berr(ALW_ENOMEM, "device allocation failed");
   if (cudaHostAlloc((void **)&b->h_state, sizeof(DevState) * n, cudaHostAllocDefault) != cudaSuccess ||
       cudaHostAlloc((void **)&b->h_done, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
     cudaGetLastError();
@@ -358,14 +385,18 @@ alw_status build(alw_batch *b) {
   memset(b->h_state, 0, sizeof(DevState) * n);
   for (int i = 0; i < n; ++i) {
     b->h_inst[i].st = b->d_state + i;
+    b->h_inst_narrow[i].st = b->d_state + i;
     b->h_state[i].t = 0.0;
     b->h_state[i].t_final = b->pend[i].t_final;
   }
   B_CUDA(cudaMemcpyAsync(b->d_inst, b->h_inst.data(), sizeof(InstDesc) * n, cudaMemcpyHostToDevice, b->stream));
+  B_CUDA(cudaMemcpyAsync(b->d_inst_narrow, b->h_inst_narrow.data(), sizeof(InstDesc) * n, cudaMemcpyHostToDevice,
+                         b->stream));
   B_CUDA(cudaMemcpyAsync(b->d_state, b->h_state, sizeof(DevState) * n, cudaMemcpyHostToDevice, b->stream));
   B_CUDA(cudaMemsetAsync(b->d_done, 0, sizeof(int), b->stream));
   // tensor maps over the whole stacked arrays
   memset(b->maps, 0, sizeof b->maps);
+  memset(b->maps_narrow, 0, sizeof b->maps_narrow);
   void *bases[6];
   int nb = 0;
   if (b->prec == P_MIXED) {
@@ -378,7 +409,8 @@ alw_status build(alw_batch *b) {
     nb = 3;
   }
   for (int i = 0; i < nb; ++i) {
-    const int r = encode_tile_map(&b->maps[i], bases[i], pitch, rows);
+    int r = encode_tile_map(&b->maps[i], bases[i], pitch, rows, kBox2DW);
+    if (r == 0) r = encode_tile_map(&b->maps_narrow[i], bases[i], pitch, rows, kBox2DWNarrow);
     if (r) return berr(ALW_ECUDA, "cuTensorMapEncodeTiled failed (%d)", r);
   }
   // split phi0 of every instance (on the device since it was added) into its block of rows with
@@ -470,6 +502,7 @@ alw_status autotune(alw_batch *b) {
   std::vector<char> live(b->h_inst.size(), 1);
   alw_batch_tuning best{};
   double best_ms = 1e30;
+  const int widths[2] = {kTile2DX, kTile2DXNarrow};
   const int orders[3] = {ALW_ORDER_INSTANCE, ALW_ORDER_LARGEST_FIRST, ALW_ORDER_INTERLEAVED};
   // runs of 4 entries per CTA: each CTA changes instance (and closes a run) a quarter as often
   // as with single entries while neighbouring blocks of tiles still run side by side (one
@@ -477,24 +510,31 @@ alw_status autotune(alw_batch *b) {
   // stages, so the run length is fixed rather than tuned)
   const int runs[1] = {kDefaultRun};
   b->tuning.grid_ctas = 0;
-  for (int o : orders)
-    for (int l : runs) {
-      alw_status st = upload_groups(b, live, o, l, nullptr);
-      if (st) return st;
-      double ms;
-      st = trial(b, 1, &ms);  // warm-up
-      if (st) return st;
-      st = trial(b, 3, &ms);
-      if (st) return st;
-      if (ms < best_ms) {
-        best_ms = ms;
-        best.order = o;
-        best.run = l;
+  for (int w : widths) {
+    b->tuning.tile_w = w;
+    b->grid_cap = cap_for(b);
+    if (b->grid_cap <= 0) continue;
+    for (int o : orders)
+      for (int l : runs) {
+        alw_status st = upload_groups(b, live, o, l, nullptr);
+        if (st) return st;
+        double ms;
+        st = trial(b, 1, &ms);  // warm-up
+        if (st) return st;
+        st = trial(b, 3, &ms);
+        if (st) return st;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best.order = o;
+          best.run = l;
+          best.tile_w = w;
+        }
       }
-    }
+  }
   best.steps_per_graph = total >= 4096 ? 2 : (total >= 512 ? 8 : 32);
   best.grid_ctas = 0;  // occupancy cap
   b->tuning = best;
+  b->grid_cap = cap_for(b);
   b->tuned = true;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune_cache[key] = best;
@@ -580,9 +620,10 @@ alw_status alw_batch_set_tuning(alw_batch *b, const alw_batch_tuning *t) {
   }
   if (t->order < ALW_ORDER_INSTANCE || t->order > ALW_ORDER_INTERLEAVED || t->steps_per_graph < 1 ||
       t->steps_per_graph > 256 || t->grid_ctas < 0 ||
-      t->run < 0 || t->run > 64)
+      t->run < 0 || t->run > 64 || (t->tile_w != 0 && t->tile_w != kTile2DX && t->tile_w != kTile2DXNarrow))
     return berr(ALW_EINVAL, "bad tuning");
   b->tuning = *t;
+  if (b->tuning.tile_w == 0) b->tuning.tile_w = kTile2DX;
   b->user_tuning = true;
   b->tuned = true;
   return ALW_OK;
@@ -616,6 +657,8 @@ alw_status alw_batch_run(alw_batch *b, int64_t *replays_out) {
     if (st) return st;
   }
   const int ninst = (int)b->h_inst.size();
+  b->grid_cap = cap_for(b);  // of the tuning's tile width
+  if (b->grid_cap <= 0) return berr(ALW_ECUDA, "stage kernel occupancy query failed");
   // live set from the device state
   B_CUDA(cudaMemcpyAsync(b->h_state, b->d_state, sizeof(DevState) * ninst, cudaMemcpyDeviceToHost, b->stream));
   B_CUDA(cudaStreamSynchronize(b->stream));
@@ -647,7 +690,7 @@ alw_status alw_batch_run(alw_batch *b, int64_t *replays_out) {
         const bool l = s.t < s.t_final && !s.err;
         live[i] = l;
         now_live += l;
-        if (l) live_tiles += b->h_inst[i].ntiles;
+        if (l) live_tiles += insts(b)[i].ntiles;
         steps_sum += s.steps;
       }
       nlive = now_live;

@@ -13,7 +13,11 @@
 //
 // Set-up: the first call on a device looks up the array's device address with
 // cudaGetSymbolAddress (with that device current) and caches it; make that
-// first call before any stream capture.  All calls on a device share the same
+// first call before any stream capture.  CUDA loads a library's device code
+// lazily by default, so that first call is also when the device code is loaded
+// on the device and the array's memory is reserved there: a caller whose pool
+// will own all device memory, or whose real-time phase must not reserve any,
+// makes the first call before that and checks its status.  All calls on a device share the same
 // array and it keeps the previous call's contents, so every call clears the
 // part it uses; calls whose GPU work overlaps (different streams, or host
 // threads without ordering between them) race on the array and must not be
@@ -93,21 +97,26 @@ extern "C" alw_status alw_step_noalloc(const alw_grid *grid, const alw_hamiltoni
   if (!(scheme->eps > 0.0) || !std::isfinite(dt) || dt < 0.0 || nsteps < 0) return err(ALW_EINVAL, "bad eps, dt or nsteps");
   if (!(grid->xhi > grid->xlo) || (grid->dim == 2 && !(grid->yhi > grid->ylo))) return err(ALW_EINVAL, "empty extent");
 
-  // layout of the scratch: state, then phi^n, stage 1 and stage 2 in the padded ghosted layout
+  // layout of the scratch: state, then phi^n, stage 1 and stage 2 in the padded ghosted layout;
+  // sizes in 64 bits until the budget check has bounded them (nx, ny up to INT_MAX)
   const int dim = grid->dim, nx = grid->nx, ny = grid->dim == 2 ? grid->ny : 1;
   const int tx = tile_x(P_F64, dim), ty = tile_y(P_F64, dim);
-  const int tiles_x = (nx + tx - 1) / tx, tiles_y = (ny + ty - 1) / ty;
-  const int pitch = tiles_x * tx + 2 * GX;
-  const int rows = dim == 2 ? tiles_y * ty + 2 * GY : 1;
-  const size_t arr = align256((size_t)pitch * rows * sizeof(double));
+  const size_t tiles_x_z = ((size_t)nx + tx - 1) / tx, tiles_y_z = ((size_t)ny + ty - 1) / ty;
+  const size_t pitch_z = tiles_x_z * tx + 2 * GX;
+  const size_t rows_z = dim == 2 ? tiles_y_z * ty + 2 * GY : 1;
   const size_t state_bytes = align256(sizeof(DevState));
+  // the product pitch_z * rows_z is formed only after both factors are bounded, so it cannot wrap
+  const bool too_big = pitch_z > kScratchBytes / sizeof(double) || rows_z > kScratchBytes / sizeof(double) ||
+                       pitch_z * rows_z > kScratchBytes / sizeof(double);
+  const size_t arr = too_big ? kScratchBytes : align256(pitch_z * rows_z * sizeof(double));
   const size_t need = state_bytes + 3 * arr;
-  if (need > kScratchBytes) {
+  if (too_big || need > kScratchBytes) {
     char buf[200];
-    snprintf(buf, sizeof buf, "grid %d x %d needs %zu bytes of working storage; the no-allocation path holds %zu",
-             nx, ny, need, kScratchBytes);
+    snprintf(buf, sizeof buf, "grid %d x %d needs more than the %zu bytes of working storage of the "
+             "no-allocation path", nx, ny, kScratchBytes);
     return err(ALW_EBUDGET, buf);
   }
+  const int tiles_x = (int)tiles_x_z, tiles_y = (int)tiles_y_z, pitch = (int)pitch_z;
   void *base = nullptr;
   alw_status st = scratch_address(&base);
   if (st) return st;

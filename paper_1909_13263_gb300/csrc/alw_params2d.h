@@ -30,6 +30,7 @@ struct Stage2DParams {
   int map_a, map_b, map_c;  // FP32: source, base (-1: none); MIXED: hi base index, lo base index, delta (-1: none)
   int ntiles;               // work-list length
   int grid_ctas;            // persistent CTAs to launch (0: as many as fit; never more than fit or ntiles)
+  int tile_w;               // tile width: 64 (0 means 64) or 32; the maps' boxes and insts[].tiles_x match it
   int batch_kind1;          // batch: 1 + the Hamiltonian every listed instance has
   const InstDesc *insts;    // batch: instance table (nullptr: the single instance `inst0`)
   DevState *states;         // batch: state of instance i at states + i (nullptr: read insts[i].st)
@@ -38,9 +39,12 @@ struct Stage2DParams {
   InstDesc inst0;
 };
 
-// TMA box of one tile with its halo (floats): 72 columns x 38 rows.
+// TMA box of one tile with its halo (floats): 72 columns x 38 rows for the 64 x 32 tile, 40 x 38
+// for the narrow 32 x 32 tile (batches may choose it).  Padded arrays are laid out for 64-wide
+// tiles, which also covers the narrow ones.
 constexpr int kBox2DW = 72, kBox2DH = 38;
 constexpr int kTile2DX = 64, kTile2DY = 32;
+constexpr int kTile2DXNarrow = 32, kBox2DWNarrow = 40;
 
 // CTAs a launch of `ntiles` work-list entries uses: min(ntiles, grid_ctas or cap, cap).
 inline int stage2d_grid(int ntiles, int grid_ctas, int cap) {
@@ -95,14 +99,21 @@ inline void cta_runs(const std::vector<int> &in, int G, std::vector<int> &out) {
 
 int launch_stage2d_f32(const Stage2DParams &prm, void *stream);
 int launch_stage2d_mixed(const Stage2DParams &prm, void *stream);
-// occupancy-limited CTA count of the persistent kernel (for work-list sizing)
-int stage2d_grid_cap_f32(int weights);
-int stage2d_grid_cap_mixed(int weights);
+// occupancy-limited CTA count of the persistent kernel (for work-list sizing), per tile width
+int stage2d_grid_cap_f32(int weights, int tile_w = kTile2DX);
+int stage2d_grid_cap_mixed(int weights, int tile_w = kTile2DX);
+// the narrow (32-wide) tile instantiations (the two entry points above dispatch to them when
+// prm.tile_w / tile_w is 32); position-free Hamiltonians only
+int launch_stage2d_f32_narrow(const Stage2DParams &prm, void *stream);
+int launch_stage2d_mixed_narrow(const Stage2DParams &prm, void *stream);
+int stage2d_grid_cap_f32_narrow(int weights);
+int stage2d_grid_cap_mixed_narrow(int weights);
 
 // Host helpers shared by the solver and batch runtimes (alw_runtime.cu).
 void *dev_alloc(size_t bytes, void *stream);
 void dev_free(void *ptr, size_t bytes, void *stream);
-// 2D float tensor map over a padded array of `pitch` x `rows` floats, box = one tile plus halo; 0 on success
-int encode_tile_map(CUtensorMap *map, void *base, long long pitch, long long rows);
+// 2D float tensor map over a padded array of `pitch` x `rows` floats, box = one tile plus halo
+// (box_w columns: kBox2DW or kBox2DWNarrow); 0 on success
+int encode_tile_map(CUtensorMap *map, void *base, long long pitch, long long rows, int box_w = kBox2DW);
 
 }  // namespace alw

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -93,12 +94,12 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder_fn() {
 }
 
 
-int alw::encode_tile_map(CUtensorMap *m, void *base, long long pitch, long long rows) {
+int alw::encode_tile_map(CUtensorMap *m, void *base, long long pitch, long long rows, int box_w) {
   auto enc = tensor_map_encoder_fn();
   if (!enc) return -1;
   const cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)kBox2DW, (cuuint32_t)kBox2DH};
+  const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)kBox2DH};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -587,6 +588,14 @@ alw_status alw_set_phi0(alw_solver *s, const double *host_phi, size_t n) {
   return st;
 }
 
+// Host-side fault injection for the no-progress check of alw_step_to: with
+// ALW_TEST_FREEZE_STATE_AFTER=n (n >= 1) in the environment, the check sees the device state as it
+// was at its n-th read, as if the device had stopped advancing; the device work is unchanged.
+static int test_freeze_after() {
+  const char *e = std::getenv("ALW_TEST_FREEZE_STATE_AFTER");
+  return e ? std::atoi(e) : 0;
+}
+
 alw_status alw_step_to(alw_solver *s, double t_final, int64_t *steps_out) {
   alw_status st = check_solver(s);
   if (st) return st;
@@ -603,6 +612,9 @@ alw_status alw_step_to(alw_solver *s, double t_final, int64_t *steps_out) {
   s->h_tf[0] = t_final;
   ALW_CUDA(cudaMemcpyAsync(&s->st->t_final, s->h_tf, sizeof(double), cudaMemcpyHostToDevice, s->stream));
   int replays = 1, stalls = 0;
+  const int freeze = test_freeze_after();
+  int reads = 0;
+  DevState frozen;
   for (;;) {
     if (!(s->h_st->t < t_final)) break;
     const double t_prev = s->h_st->t;
@@ -610,6 +622,10 @@ alw_status alw_step_to(alw_solver *s, double t_final, int64_t *steps_out) {
     for (int r = 0; r < replays; ++r) ALW_CUDA(cudaGraphLaunch(s->g_step, s->stream));
     st = read_state(s);
     if (st) return st;
+    if (freeze > 0 && ++reads >= freeze) {
+      if (reads == freeze) frozen = *s->h_st;
+      else *s->h_st = frozen;
+    }
     // the device must make progress on every replay batch; never loop on a stuck state
     if (!s->h_st->err && s->h_st->steps == steps_prev && s->h_st->t == t_prev) {
       if (++stalls >= 3) return fail(ALW_ETIMEOUT, "no progress at t = %.17g", s->h_st->t);

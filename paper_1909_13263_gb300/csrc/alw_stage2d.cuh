@@ -33,22 +33,33 @@
 
 namespace alw {
 
-// Hamiltonians of the 2D examples in float (compile-time kind).
+// Hamiltonians of the 2D examples in float (compile-time kind).  value_sums takes the sums
+// su = u^- + u^+, sv = v^- + v^+ (the Lax-Friedrichs flux evaluates H at (su/2, sv/2)); kSameAlpha
+// marks Hamiltonians whose node alpha is the same in both directions.
 template <int H> struct Ham2;
 template <> struct Ham2<H_BURGERS2D> {
+  static constexpr bool kSameAlpha = true;
   __device__ __forceinline__ static float value(float p, float q, float, float) {
     const float z = p + q + 1.0f;
     return 0.5f * z * z;
   }
+  __device__ __forceinline__ static float value_sums(float su, float sv, float, float) {
+    const float z = fmaf(0.5f, su + sv, 1.0f);
+    return 0.5f * z * z;
+  }
   __device__ __forceinline__ static void alpha(float um, float up, float vm, float vp, float, float, float &ax,
                                                     float &ay) {
-    const float a = fabsf(um + vm + 1.0f), b = fabsf(um + vp + 1.0f);
-    const float c = fabsf(up + vm + 1.0f), d = fabsf(up + vp + 1.0f);
-    ax = ay = fmaxf(fmaxf(a, b), fmaxf(c, d));
+    // |H_p| = |H_q| = |u + v + 1| at the four corners (u + 1 shared by two of them)
+    const float u0 = um + 1.0f, u1 = up + 1.0f;
+    ax = ay = fmaxf(fmaxf(fabsf(u0 + vm), fabsf(u0 + vp)), fmaxf(fabsf(u1 + vm), fabsf(u1 + vp)));
   }
 };
 template <> struct Ham2<H_NEGCOS2D> {
+  static constexpr bool kSameAlpha = true;
   __device__ __forceinline__ static float value(float p, float q, float, float) { return -sfu_cos(p + q + 1.0f); }
+  __device__ __forceinline__ static float value_sums(float su, float sv, float, float) {
+    return -sfu_cos(fmaf(0.5f, su + sv, 1.0f));
+  }
   __device__ __forceinline__ static void alpha(float um, float up, float vm, float vp, float, float, float &ax,
                                                     float &ay) {
     const float a = fabsf(sfu_sin(um + vm + 1.0f)), b = fabsf(sfu_sin(um + vp + 1.0f));
@@ -57,7 +68,11 @@ template <> struct Ham2<H_NEGCOS2D> {
   }
 };
 template <> struct Ham2<H_SIN2D> {
+  static constexpr bool kSameAlpha = true;
   __device__ __forceinline__ static float value(float p, float q, float, float) { return sfu_sin(p + q); }
+  __device__ __forceinline__ static float value_sums(float su, float sv, float, float) {
+    return sfu_sin(0.5f * (su + sv));
+  }
   __device__ __forceinline__ static void alpha(float um, float up, float vm, float vp, float, float, float &ax,
                                                     float &ay) {
     const float a = fabsf(sfu_cos(um + vm)), b = fabsf(sfu_cos(um + vp));
@@ -66,6 +81,10 @@ template <> struct Ham2<H_SIN2D> {
   }
 };
 template <> struct Ham2<H_EIKONAL2D> {
+  static constexpr bool kSameAlpha = false;
+  __device__ __forceinline__ static float value_sums(float su, float sv, float x, float y) {
+    return value(0.5f * su, 0.5f * sv, x, y);
+  }
   __device__ __forceinline__ static float value(float p, float q, float, float) {
     const float t = fmaf(p, p, fmaf(q, q, 1.0f));   // >= 1
     return t * sfu_rsqrt(t);
@@ -81,6 +100,10 @@ template <> struct Ham2<H_EIKONAL2D> {
 
 // Example 11 (optimal control): the only Hamiltonian that depends on the node position (x, y).
 template <> struct Ham2<H_OPTCTRL2D> {
+  static constexpr bool kSameAlpha = false;
+  __device__ __forceinline__ static float value_sums(float su, float sv, float x, float y) {
+    return value(0.5f * su, 0.5f * sv, x, y);
+  }
   __device__ __forceinline__ static float value(float p, float q, float x, float y) {
     const float sx = sfu_sin(x), cx = sfu_cos(x), sy = sfu_sin(y);
     // sin(y) p + (sin(x) + sign q) q - sin^2(y)/2 - (1 - cos x), with (sign q) q = |q|
@@ -97,8 +120,9 @@ template <> struct Ham2<H_OPTCTRL2D> {
 
 // The Hamiltonian of a launch (compile-time kind; batches launch one group per Hamiltonian).
 template <int H> struct HamSel {
-  __device__ __forceinline__ float value(float p, float q, float x, float y) const {
-    return Ham2<H>::value(p, q, x, y);
+  static constexpr bool kSameAlpha = Ham2<H>::kSameAlpha;
+  __device__ __forceinline__ float value_sums(float su, float sv, float x, float y) const {
+    return Ham2<H>::value_sums(su, sv, x, y);
   }
   __device__ __forceinline__ void alpha(float um, float up, float vm, float vp, float x, float y, float &ax,
                                         float &ay) const {
@@ -106,17 +130,24 @@ template <int H> struct HamSel {
   }
 };
 
+// Tile geometry of the stage kernel for tiles TXv nodes wide and 32 high (64 or 32 wide): one thread
+// per 8-node row segment and 8-node column segment, so TXv / 8 warps; the TMA box is the tile plus
+// its halo (4 columns, 3 rows each side); 8 warps per SM per 32 columns of tile width.
+template <int TXv>
 struct Geo2D {
-  static constexpr int TX = kTile2DX, TY = kTile2DY, K = 8, NT = 256;
+  static constexpr int TX = TXv, TY = kTile2DY, K = 8, NT = TX * TY / K;
+  static constexpr int MINB = 512 / NT;                 // resident CTAs per SM the registers are sized for
+  static constexpr int CG = TX / 32;                    // column groups of 32 in the y sweep
   static constexpr int SW = TX + 8, SH = TY + 6;        // TMA box (halo 4 columns / 3 rows each side)
   static constexpr int ARR = ((SH * SW + 31) / 32) * 32; // floats per array slot (128-byte multiple)
-  static constexpr int DXW = TX + 5, DXP = 73;          // x differences: width, odd pitch
+  static constexpr int DXW = TX + 5, DXP = TX + 9;      // x differences: width, odd pitch
   static constexpr int SUP = TX + 1;                    // phi_x^-/+ pitch in float2
   template <int NARR> static constexpr size_t smem_bytes() {
     return 128 + sizeof(float) * (size_t)(2 * NARR * ARR + TY * DXP) + sizeof(float2) * (size_t)TY * SUP;
   }
 };
-static_assert(Geo2D::SW == kBox2DW && Geo2D::SH == kBox2DH, "TMA box must match the tile halo");
+static_assert(Geo2D<kTile2DX>::SW == kBox2DW && Geo2D<kTile2DX>::SH == kBox2DH, "TMA box must match the tile halo");
+static_assert(Geo2D<kTile2DXNarrow>::SW == kBox2DWNarrow, "TMA box must match the tile halo");
 
 // Everything a tile needs from its instance, gathered by thread 0 into shared memory when the
 // tile is prepared (one tile ahead), so that the compute phase reads no instance data from
@@ -130,12 +161,17 @@ struct TileInfo {
   DevState *st;
 };
 
-template <int PREC, int W, int H>
-__global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_constant__ Stage2DParams prm) {
-  constexpr int TX = Geo2D::TX, TY = Geo2D::TY, K = Geo2D::K, NT = Geo2D::NT;
-  constexpr int SW = Geo2D::SW, SH = Geo2D::SH, ARR = Geo2D::ARR;
-  constexpr int DXW = Geo2D::DXW, DXP = Geo2D::DXP, SUP = Geo2D::SUP;
+template <int PREC, int W, int H, int TXv>
+__global__ void __launch_bounds__(Geo2D<TXv>::NT, Geo2D<TXv>::MINB)
+    stage2d_kernel(const __grid_constant__ Stage2DParams prm) {
+  using G = Geo2D<TXv>;
+  constexpr int TX = G::TX, TY = G::TY, K = G::K, NT = G::NT;
+  constexpr int SW = G::SW, SH = G::SH, ARR = G::ARR;
+  constexpr int DXW = G::DXW, DXP = G::DXP, SUP = G::SUP, CG = G::CG;
   constexpr int NARR = (PREC == P_MIXED) ? 3 : 2;
+  // arc length with the increment form (MIXED): try the short-interval sweep first (FP32 stores phi
+  // itself, whose rounding makes second differences rough at fine grids, so it never qualifies there)
+  constexpr bool SHORT = (W == W_ARCLEN && PREC == P_MIXED);
   const StageParams &p = prm.p;
   const bool batch = prm.insts != nullptr;
   if (!batch) {
@@ -298,7 +334,7 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
   int k = 0;
   // running alpha maxima and tile count of the current run of same-instance tiles
   float amx = 0.0f, amy = 0.0f;
-  bool bad = false;
+  float nfin = 0.0f;  // NaN once a non-finite L was met (see the finish loop)
   int run_tiles = 0;
   // thread 0: work-list entry of the tile after next, loaded one tile ahead of its use
   int e_ahead = (batch && tid == 0 && (int)(blockIdx.x + gridDim.x) < ntiles) ? prm.tiles[blockIdx.x + gridDim.x] : 0;
@@ -379,7 +415,7 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
     prepare_next(next, buf);
 
     const bool edge = (tx0 < 3) || (tx0 + TX > nx - 3) || (ty0 < 3) || (ty0 + TY > ny - 3);
-    const int colY = ((warp & 1) << 5) + lane, segY = warp >> 1;
+    const int colY = (warp % CG) * 32 + lane, segY = warp / CG;
 
     // ---- 2. both sweeps in one pass: each thread's row segment (x, lane .x of the packed values)
     // and column segment (y, lane .y) run the same instruction stream
@@ -390,26 +426,29 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
       // differences of the differences pass; v_at is called for m = 0, 1, 2, ... in order, so each
       // position loads one new row and reuses the previous one
       const int iy = (K * segY) * SW + colY + 4;
-      float pa = A[iy], pb = 0.0f, pc = 0.0f;
-      if (PREC == P_MIXED) {
-        pb = B[iy];
-        pc = C[iy];
-      }
-      auto v_at = [&](int m) {
-        const int i1 = iy + (m + 1) * SW;
-        float dy;
+      const float rdy = d.rdy;
+      auto make_vat = [&]() {
+        float pa = A[iy], pb = 0.0f, pc = 0.0f;
         if (PREC == P_MIXED) {
-          const float a1 = A[i1], b1 = B[i1], c1 = C[i1];
-          dy = (a1 - pa) + ((b1 - pb) + (c1 - pc));
-          pa = a1;
-          pb = b1;
-          pc = c1;
-        } else {
-          const float a1 = A[i1];
-          dy = a1 - pa;
-          pa = a1;
+          pb = B[iy];
+          pc = C[iy];
         }
-        return make_float2(vx[m], dy * d.rdy);
+        return [=](int m) mutable {
+          const int i1 = iy + (m + 1) * SW;
+          float dy;
+          if (PREC == P_MIXED) {
+            const float a1 = A[i1], b1 = B[i1], c1 = C[i1];
+            dy = (a1 - pa) + ((b1 - pb) + (c1 - pc));
+            pa = a1;
+            pb = b1;
+            pc = c1;
+          } else {
+            const float a1 = A[i1];
+            dy = a1 - pa;
+            pa = a1;
+          }
+          return make_float2(vx[m], dy * rdy);
+        };
       };
       auto emit = [&](int q, float2 dm, float2 dp) {
         su[lane * SUP + K * warp + q] = make_float2(dm.x, dp.x);
@@ -418,7 +457,15 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
       };
       const float2 rd = make_float2(d.rdx, d.rdy);
       const float2 e4 = make_float2(4.0f * eps * d.rdx * d.rdx, 4.0f * eps * d.rdy * d.rdy);
-      sweep_stream<K, W, float2>(v_at, rd, e4, make_float2(eps, eps), emit);
+      // arc length, MIXED: every warp sweeps with the short-interval form first and sweeps again in
+      // full when some segment of the warp does not qualify (that form then replaces all its
+      // results).  Which form produced a node's values thus depends only on the data of the warp's
+      // segments, whose position on the grid is fixed by the tile width -- not on the order in
+      // which tiles or instances are processed, nor on history: a single solve, a batch, a server
+      // round and a resumed checkpoint (all with 64-wide tiles) choose alike.
+      bool full = true;
+      if (SHORT) full = !sweep_stream_short<K, float2>(make_vat(), rd, e4, emit);
+      if (full) sweep_stream<K, W, float2>(make_vat(), rd, e4, make_float2(eps, eps), emit);
     }
     __syncthreads();
 
@@ -438,12 +485,13 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
         float ax, ay;
         ham.alpha(u.x, u.y, dmq, dpq, xn, yn, ax, ay);
         const float aX = local_alpha ? ax : fax, aY = local_alpha ? ay : fay;
-        const float Hv = ham.value(0.5f * (u.y + u.x), 0.5f * (dpq + dmq), xn, yn);
+        const float Hv = ham.value_sums(u.y + u.x, dpq + dmq, xn, yn);
         const float L = fmaf(aX * 0.5f, u.y - u.x, fmaf(aY * 0.5f, dpq - dmq, -Hv));
         if (inside) {
-          if (!isfinite(L)) bad = true;   // L depends on all four one-sided derivatives
+          // L depends on all four one-sided derivatives: L * 0 is NaN exactly when L is not finite
+          nfin = fmaf(L, 0.0f, nfin);
           amx = fmaxf(amx, ax);
-          amy = fmaxf(amy, ay);
+          if (!HamSel<H>::kSameAlpha) amy = fmaxf(amy, ay);
         }
         if (ST == 0 || !inside) continue;
         const int sidx = (y + 3) * SW + colY + 4;
@@ -505,12 +553,13 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
       // tile's first barrier, which every thread reaches after finishing this tile
       continue;
     }
+    if (HamSel<H>::kSameAlpha) amy = amx;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       amx = fmaxf(amx, __shfl_xor_sync(0xffffffffu, amx, o));
       amy = fmaxf(amy, __shfl_xor_sync(0xffffffffu, amy, o));
     }
-    const int anybad = __syncthreads_or(bad ? 1 : 0);
+    const int anybad = __syncthreads_or(nfin != nfin ? 1 : 0);
     if (lane == 0) {
       s_red[0][warp] = amx;
       s_red[1][warp] = amy;
@@ -553,7 +602,7 @@ __global__ void __launch_bounds__(Geo2D::NT, 2) stage2d_kernel(const __grid_cons
       }
     }
     amx = amy = 0.0f;
-    bad = false;
+    nfin = 0.0f;
     run_tiles = 0;
     __syncthreads();  // raw[buf], dX, su, s_info[buf] are free for the next tile
   }

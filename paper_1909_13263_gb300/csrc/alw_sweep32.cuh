@@ -22,30 +22,75 @@
 //   omega_0 = A0 / den, omega_2 = 3 A2 / den,
 //   phi^- = (c + T_b/12) - (A0 T_a / 3 + A2 T_b / 2) / den,
 //   phi^+ = (c - T_b/12) + (A0' T_c / 3 + A2' T_b / 2) / den'.
+//
+// Short intervals.  The interval mean G takes the trapezoid value (s_a + s_b) / 2 whenever the
+// interval [a, b] is short against its end values (|b - a| <= (s_a + s_b) / 64, s = sqrt(1 + u^2)).
+// On smooth data at fine grids every interval of a segment is that short (its width is a third
+// difference of phi over dx^2, about phi_xxx dx), and then F, its logarithm and the interval
+// reciprocals are never used.  sweep_stream_short computes only what the trapezoid branch needs
+// and reports whether the segment qualifies: every width D2_{m+1} - D2_m of the segment at most
+// kShortH (which implies the trapezoid branch for all three interval kinds, because
+// R_m - D2_m = D2_m - D2_{m-1} and D2_m - L_m = D2_{m+1} - D2_m up to one rounding of R or L,
+// and s >= 1), |D2| at the segment start at most kShortD2 and eps4 at most kShortEps4 (together
+// these keep every weight denominator below 1e29, so the overflow branch of side_corr_v cannot be
+// taken).  When the segment qualifies, both sweeps evaluate the same formulas on the same branches;
+// their results agree to rounding (the compiler may select instructions for the two code paths
+// differently), and the stage kernel decides between them from the segment's own data only.
 #pragma once
 #include "alw_device.cuh"
 
 namespace alw {
 
+constexpr float kShortH = 0.03f;      // largest width D2_{m+1} - D2_m of a short segment
+constexpr float kShortD2 = 400.0f;    // largest |D2| at the start of a short segment
+constexpr float kShortEps4 = 1.0e6f;  // largest 4 eps / dx^2 of a short segment
+
 // ---- lane-wise operations on float and float2 ------------------------------------------
-__device__ __forceinline__ float vadd(float a, float b) { return a + b; }
-__device__ __forceinline__ float vsub(float a, float b) { return a - b; }
-__device__ __forceinline__ float vmul(float a, float b) { return a * b; }
+// Every add, subtract and multiply is rounded as written: the packed forms are PTX instructions
+// with an explicit rounding mode, which the compiler does not contract into a fused multiply-add
+// (the f32x2 intrinsics were contracted with a following subtraction in some contexts and not
+// in others).  Fused multiply-adds are written as vfma.
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ float vsplat(float x, float) { return x; }
-__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
-__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) {
+  float2 r;
+  asm("{\n .reg .b64 a, b, d;\n mov.b64 a, {%2, %3};\n mov.b64 b, {%4, %5};\n add.rn.f32x2 d, a, b;\n"
+      " mov.b64 {%0, %1}, d;\n}"
+      : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) {
+  float2 r;
+  asm("{\n .reg .b64 a, b, d;\n mov.b64 a, {%2, %3};\n mov.b64 b, {%4, %5};\n sub.rn.f32x2 d, a, b;\n"
+      " mov.b64 {%0, %1}, d;\n}"
+      : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) {
+  float2 r;
+  asm("{\n .reg .b64 a, b, d;\n mov.b64 a, {%2, %3};\n mov.b64 b, {%4, %5};\n mul.rn.f32x2 d, a, b;\n"
+      " mov.b64 {%0, %1}, d;\n}"
+      : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
 __device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 vsplat(float x, float2) { return make_float2(x, x); }
 
 // Special-function-unit approximations in their flush-to-zero PTX forms (reciprocal square root,
-// base-2 logarithm, reciprocal).  No input here is subnormal -- 1 + u^2 >= 1, |u| + sqrt(1 + u^2) >= 1,
+// square root, base-2 logarithm, reciprocal).  No input here is subnormal -- 1 + u^2 >= 1, |u| + sqrt(1 + u^2) >= 1,
 // weight denominators >= 1e-24 -- except 1/h for a vanishing interval, whose quotient the trapezoid
 // branch discards, so the results equal those of the non-flushing forms.
 __device__ __forceinline__ float sfu_rsqrt(float x) {
   float r;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float sfu_sqrt(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
 __device__ __forceinline__ float sfu_lg2(float x) {
@@ -87,15 +132,24 @@ template <class V> struct FValV {
   V F, s;  // F(u) = u sqrt(1+u^2) + asinh(u), s = sqrt(1+u^2)
 };
 
+// s = sqrt(1 + u^2) as one square-root instruction per lane (a single rounding step, so that every
+// code path that evaluates it gets the same bits)
+template <class V>
+__device__ __forceinline__ V s_eval_v(V u) {
+  using LN = Lanes<V>;
+  const V t = vfma(u, u, vsplat(1.0f, u));
+  V r;
+#pragma unroll
+  for (int i = 0; i < LN::n; ++i) LN::at(r, i) = sfu_sqrt(LN::get(t, i));
+  return r;
+}
+
 template <class V>
 __device__ __forceinline__ FValV<V> f_eval_v(V u) {
   using LN = Lanes<V>;
   FValV<V> r;
-  const V t = vfma(u, u, vsplat(1.0f, u));
-  V rs, lsg;
-#pragma unroll
-  for (int i = 0; i < LN::n; ++i) LN::at(rs, i) = sfu_rsqrt(LN::get(t, i));
-  r.s = vmul(t, rs);
+  V lsg;
+  r.s = s_eval_v(u);
   // |u| + s per lane (the absolute value is an operand modifier of the scalar add)
 #pragma unroll
   for (int i = 0; i < LN::n; ++i)
@@ -135,9 +189,12 @@ static __device__ __noinline__ float side_corr_wide(float q0, float q1, float q2
   return (a0 * r) * ta3 + (a2 * r) * (1.0f / 3.0f) * tb2;
 }
 
-// The side's correction (A0 T_a / 3 + A2 T_b / 2) / den; ta3 = T_a / 3, tb2 = T_b / 2.
+// The side's correction (A0 T_a / 3 + A2 T_b / 2) / den as a pair (num, r) with correction =
+// num * r (r = 1 / den; on the rare lanes whose products leave the float range, num = the
+// correction and r = 1); ta3 = T_a / 3, tb2 = T_b / 2 (both negated for the "-" side, whose
+// correction is subtracted).  The caller adds it to the central part with one fused multiply-add.
 template <class V>
-__device__ __forceinline__ V side_corr_v(V q0, V q1, V q2, V ta3, V tb2) {
+__device__ __forceinline__ void side_corr_v(V q0, V q1, V q2, V ta3, V tb2, V &num_out, V &r_out) {
   using LN = Lanes<V>;
   const V A0 = vmul(q1, q2), A1 = vmul(q0, q2), A2 = vmul(q0, q1);
   const V den = vfma(vsplat(6.0f, q0), A1, vfma(vsplat(3.0f, q0), A2, A0));
@@ -152,21 +209,53 @@ __device__ __forceinline__ V side_corr_v(V q0, V q1, V q2, V ta3, V tb2) {
     ok = ok && (dn < 1e30f);
     LN::at(rd, i) = sfu_rcp(dn);
   }
-  V out = vmul(num, rd);
+  V nm = num;
   if (!ok) {
 #pragma unroll
     for (int i = 0; i < LN::n; ++i) {
       const float dn = LN::get(den, i);
-      if (!(dn < 1e30f))
-        LN::at(out, i) = side_corr_wide(LN::get(q0, i), LN::get(q1, i), LN::get(q2, i), LN::get(ta3, i),
-                                        LN::get(tb2, i));
+      if (!(dn < 1e30f)) {
+        LN::at(nm, i) = side_corr_wide(LN::get(q0, i), LN::get(q1, i), LN::get(q2, i), LN::get(ta3, i),
+                                       LN::get(tb2, i));
+        LN::at(rd, i) = 1.0f;
+      }
     }
   }
-  return out;
+  num_out = nm;
+  r_out = rd;
 }
 
 // v_at(m) returns Delta^+ phi at position i0 - 3 + m (m = 0..K+4) per lane; emit(p, dm, dp)
 // receives node i0 + p.  rdx = 1/dx, eps4 = 4 eps / dx^2 (per lane).
+// Every lane of v holds a width at most kShortH (NaN fails).
+template <class V>
+__device__ __forceinline__ bool short_width(V h) {
+  using LN = Lanes<V>;
+  bool ok = true;
+#pragma unroll
+  for (int i = 0; i < LN::n; ++i) ok &= fabsf(LN::get(h, i)) <= kShortH;
+  return ok;
+}
+
+// The size conditions of a short segment on |D2| at its start and on eps4 (NaN fails).
+template <class V>
+__device__ __forceinline__ bool short_sizes(V d2, V eps4) {
+  using LN = Lanes<V>;
+  bool ok = true;
+#pragma unroll
+  for (int i = 0; i < LN::n; ++i)
+    ok &= (fabsf(LN::get(d2, i)) <= kShortD2) & (LN::get(eps4, i) <= kShortEps4);
+  return ok;
+}
+
+// The extrapolated interval ends R_m = 2 D2_m - D2_{m-1} and L_m = 2 D2_m - D2_{m+1}, formed as
+// D2_m plus or minus the neighbouring width (the widths are the quantities the short-interval test
+// inspects; one operation each).
+template <class V>
+__device__ __forceinline__ V r_end(V d2m, V d2prev) { return vadd(d2m, vsub(d2m, d2prev)); }
+template <class V>
+__device__ __forceinline__ V l_end(V d2m, V d2next) { return vsub(d2m, vsub(d2next, d2m)); }
+
 template <int K, int WEIGHTS, class V, class LoadV, class Emit>
 __device__ __forceinline__ void sweep_stream(LoadV v_at, V rdx, V eps4, V eps, Emit emit) {
   V v[K + 5];
@@ -175,7 +264,7 @@ __device__ __forceinline__ void sweep_stream(LoadV v_at, V rdx, V eps4, V eps, E
   V qX[K + 6], qY[K + 6], qZ[K + 6];
   V D2[K + 6];
   FValV<V> FD[K + 6];
-  const V two = vsplat(2.0f, eps), mtwo = vsplat(-2.0f, eps);
+  const V mtwo = vsplat(-2.0f, eps);
 
   auto pos_s = [&](int m) {                  // s, and D2 for arc length
     s[m] = vsub(v[m], v[m - 1]);
@@ -183,12 +272,12 @@ __device__ __forceinline__ void sweep_stream(LoadV v_at, V rdx, V eps4, V eps, E
   };
   auto pos_T = [&](int m) { T[m] = vfma(mtwo, s[m], vadd(s[m - 1], s[m + 1])); };
   auto al_qX = [&](int m) {                  // interval (D2_m, R_m), R = 2 D2_m - D2_{m-1}
-    const V R = vsub(vmul(two, D2[m]), D2[m - 1]);
+    const V R = r_end(D2[m], D2[m - 1]);
     qX[m] = q_interval_v(D2[m], FD[m], R, f_eval_v(R), eps4);
   };
   auto al_qY = [&](int m) { qY[m] = q_interval_v(D2[m], FD[m], D2[m + 1], FD[m + 1], eps4); };
   auto al_qZ = [&](int m) {                  // interval (L_m, D2_m), L = 2 D2_m - D2_{m+1}
-    const V Lv = vsub(vmul(two, D2[m]), D2[m + 1]);
+    const V Lv = l_end(D2[m], D2[m + 1]);
     qZ[m] = q_interval_v(Lv, f_eval_v(Lv), D2[m], FD[m], eps4);
   };
   auto jp_pair = [&](int m) {                // Jiang-Peng quantities of the pair (s_m, s_{m+1})
@@ -221,23 +310,23 @@ __device__ __forceinline__ void sweep_stream(LoadV v_at, V rdx, V eps4, V eps, E
     for (int m = 1; m <= 4; ++m) jp_pair(m);
   }
 
-  const V c712 = vsplat(7.0f / 12.0f, eps), cm112 = vsplat(-1.0f / 12.0f, eps);
-  const V c13 = vsplat(1.0f / 3.0f, eps), c12 = vsplat(0.5f, eps);
+  const V c712 = vsplat(7.0f / 12.0f, eps), cm112 = vsplat(-1.0f / 12.0f, eps), c112 = vsplat(1.0f / 12.0f, eps);
+  const V c13 = vsplat(1.0f / 3.0f, eps), cm13 = vsplat(-1.0f / 3.0f, eps);
+  const V c12 = vsplat(0.5f, eps), cm12 = vsplat(-0.5f, eps);
 #pragma unroll
   for (int p = 0; p < K; ++p) {
-    // node p
+    // node p: phi^- = (c + T_b/12) - corr^-, phi^+ = (c - T_b/12) + corr^+
     const V c = vfma(c712, vadd(v[p + 2], v[p + 3]), vmul(cm112, vadd(v[p + 1], v[p + 4])));
     const V tb = T[p + 3];
-    const V tb12 = vmul(tb, vsplat(1.0f / 12.0f, eps)), tb2 = vmul(c12, tb);
-    V cm, cp;
+    V nm, rm, np, rp;
     if (WEIGHTS == W_ARCLEN) {
-      cm = side_corr_v(qX[p + 2], qY[p + 2], qZ[p + 3], vmul(T[p + 2], c13), tb2);
-      cp = side_corr_v(qZ[p + 4], qY[p + 3], qX[p + 3], vmul(T[p + 4], c13), tb2);
+      side_corr_v(qX[p + 2], qY[p + 2], qZ[p + 3], vmul(T[p + 2], cm13), vmul(cm12, tb), nm, rm);
+      side_corr_v(qZ[p + 4], qY[p + 3], qX[p + 3], vmul(T[p + 4], c13), vmul(c12, tb), np, rp);
     } else {
-      cm = side_corr_v(qX[p + 1], qY[p + 2], qZ[p + 3], vmul(T[p + 2], c13), tb2);
-      cp = side_corr_v(qZ[p + 4], qY[p + 3], qX[p + 2], vmul(T[p + 4], c13), tb2);
+      side_corr_v(qX[p + 1], qY[p + 2], qZ[p + 3], vmul(T[p + 2], cm13), vmul(cm12, tb), nm, rm);
+      side_corr_v(qZ[p + 4], qY[p + 3], qX[p + 2], vmul(T[p + 4], c13), vmul(c12, tb), np, rp);
     }
-    emit(p, vsub(vadd(c, tb12), cm), vadd(vsub(c, tb12), cp));
+    emit(p, vfma(nm, rm, vfma(tb, c112, c)), vfma(np, rp, vfma(tb, cm112, c)));
     // advance the window by one position
     if (p + 1 < K) {
       v[p + 6] = v_at(p + 6);
@@ -253,6 +342,86 @@ __device__ __forceinline__ void sweep_stream(LoadV v_at, V rdx, V eps4, V eps, E
       }
     }
   }
+}
+
+// Arc-length sweep of segments on which every interval takes the trapezoid branch (see the header
+// comment): the square roots s = sqrt(1 + u^2) of the interval ends, the trapezoid values and the
+// weights, with the operations of sweep_stream on those branches.  Called by all 32 threads of a
+// warp; returns, uniformly across the warp, whether every segment of the warp (both lanes of all
+// threads) met the conditions (checked after the prologue, where a failing warp stops at once,
+// and after the last node).  When it returns false the emitted values, if any, are not to be
+// used and the caller sweeps the warp's segments again with sweep_stream.
+template <int K, class V, class LoadV, class Emit>
+__device__ __forceinline__ bool sweep_stream_short(LoadV v_at, V rdx, V eps4, Emit emit) {
+  using LN = Lanes<V>;
+  V v[K + 5];
+  V s[K + 5];
+  V T[K + 5];
+  V D2[K + 6];
+  V S[K + 6];                                // S_m = sqrt(1 + D2_m^2)
+  V qX[K + 6], qY[K + 6], qZ[K + 6];
+  const V mtwo = vsplat(-2.0f, rdx);
+  bool ok = true;
+
+  auto sq = [&](V u) { return s_eval_v(u); };   // FValV::s of f_eval_v
+  auto qv = [&](V sa, V sb) {                // q of q_interval_v on its trapezoid branch
+    const V ss = vadd(sa, sb);
+    const V e = vfma(ss, ss, eps4);
+    return vmul(e, e);
+  };
+  auto pos_s = [&](int m) {
+    s[m] = vsub(v[m], v[m - 1]);
+    D2[m] = vmul(s[m], rdx);
+    if (m >= 2) ok &= short_width(vsub(D2[m], D2[m - 1]));
+  };
+  auto pos_T = [&](int m) { T[m] = vfma(mtwo, s[m], vadd(s[m - 1], s[m + 1])); };
+  auto al_qX = [&](int m) { qX[m] = qv(S[m], sq(r_end(D2[m], D2[m - 1]))); };
+  auto al_qY = [&](int m) { qY[m] = qv(S[m], S[m + 1]); };
+  auto al_qZ = [&](int m) { qZ[m] = qv(sq(l_end(D2[m], D2[m + 1])), S[m]); };
+  // side_corr_v when the denominator is known to be in range
+  auto corr = [&](V q0, V q1, V q2, V ta3, V tb2, V &num, V &rd) {
+    const V A0 = vmul(q1, q2), A1 = vmul(q0, q2), A2 = vmul(q0, q1);
+    const V den = vfma(vsplat(6.0f, q0), A1, vfma(vsplat(3.0f, q0), A2, A0));
+    num = vfma(A0, ta3, vmul(A2, tb2));
+#pragma unroll
+    for (int i = 0; i < LN::n; ++i) LN::at(rd, i) = sfu_rcp(LN::get(den, i));
+  };
+
+#pragma unroll
+  for (int m = 0; m <= 5; ++m) v[m] = v_at(m);
+#pragma unroll
+  for (int m = 1; m <= 5; ++m) pos_s(m);
+#pragma unroll
+  for (int m = 2; m <= 4; ++m) pos_T(m);
+#pragma unroll
+  for (int m = 2; m <= 4; ++m) S[m] = sq(D2[m]);
+  al_qX(2); al_qY(2); al_qZ(3);
+  al_qX(3); al_qY(3); al_qZ(4);
+  ok &= short_sizes(D2[2], eps4);
+  if (!__all_sync(0xffffffffu, ok)) return false;
+
+  const V c712 = vsplat(7.0f / 12.0f, rdx), cm112 = vsplat(-1.0f / 12.0f, rdx), c112 = vsplat(1.0f / 12.0f, rdx);
+  const V c13 = vsplat(1.0f / 3.0f, rdx), cm13 = vsplat(-1.0f / 3.0f, rdx);
+  const V c12 = vsplat(0.5f, rdx), cm12 = vsplat(-0.5f, rdx);
+#pragma unroll
+  for (int p = 0; p < K; ++p) {
+    const V c = vfma(c712, vadd(v[p + 2], v[p + 3]), vmul(cm112, vadd(v[p + 1], v[p + 4])));
+    const V tb = T[p + 3];
+    V nm, rm, np, rp;
+    corr(qX[p + 2], qY[p + 2], qZ[p + 3], vmul(T[p + 2], cm13), vmul(cm12, tb), nm, rm);
+    corr(qZ[p + 4], qY[p + 3], qX[p + 3], vmul(T[p + 4], c13), vmul(c12, tb), np, rp);
+    emit(p, vfma(nm, rm, vfma(tb, c112, c)), vfma(np, rp, vfma(tb, cm112, c)));
+    if (p + 1 < K) {
+      v[p + 6] = v_at(p + 6);
+      pos_s(p + 6);
+      pos_T(p + 5);
+      S[p + 5] = sq(D2[p + 5]);
+      al_qX(p + 4);
+      al_qY(p + 4);
+      al_qZ(p + 5);
+    }
+  }
+  return __all_sync(0xffffffffu, ok);
 }
 
 }  // namespace alw

@@ -65,7 +65,7 @@ class State(ctypes.Structure):
 
 class BatchTuning(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int32), ("steps_per_graph", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
-                ("run", ctypes.c_int32)]
+                ("run", ctypes.c_int32), ("tile_w", ctypes.c_int32)]
 
 
 ORDER = {"instance": 0, "largest_first": 1, "interleaved": 2}
@@ -323,10 +323,16 @@ def step_noalloc(phi_in, phi_out, *, dim: int, nx: int, ny: int = 1, bc: str = "
                  alpha_mode: str = "default", alpha_fixed=(0.0, 0.0), dt: float, nsteps: int = 1, stream=None):
     """alw_step_noalloc: nsteps FP64 RK3 steps of fixed dt on caller-owned CUDA float64 tensors,
     using the library's fixed working storage instead of allocating device memory."""
+    import torch
+
     L = load()
     for t in (phi_in, phi_out):
         if not (t.is_cuda and str(t.dtype) == "torch.float64" and t.is_contiguous() and t.numel() == nx * ny):
             raise AlwError(EINVAL, "phi_in/phi_out must be contiguous CUDA float64 tensors of nx*ny values")
+        # the library works on the current device: its kernels there must not address another GPU's memory
+        if t.device.index != torch.cuda.current_device():
+            raise AlwError(EINVAL, f"tensor on cuda:{t.device.index}, but the current device is "
+                                   f"cuda:{torch.cuda.current_device()}")
     g = Grid(dim, nx, ny if dim == 2 else 1, BC[bc], xlo, xhi, ylo, yhi)
     h = Hamiltonian(HAM[ham], (ctypes.c_double * 4)(0, 0, 0, 0))
     s = Scheme(WEIGHTS[weights], eps, 0.6, DT["cfl"], ALPHA[alpha_mode], (ctypes.c_double * 2)(*alpha_fixed),
@@ -362,11 +368,12 @@ class Batch:
         self.shapes.append((ny, nx))
         return i.value
 
-    def set_tuning(self, order: str = None, steps_per_graph: int = 4, grid_ctas: int = 0, run: int = 4):
+    def set_tuning(self, order: str = None, steps_per_graph: int = 4, grid_ctas: int = 0, run: int = 4,
+                   tile_w: int = 64):
         if order is None:
             check(self._L.alw_batch_set_tuning(self._h, None))
             return
-        t = BatchTuning(ORDER[order], steps_per_graph, grid_ctas, run)
+        t = BatchTuning(ORDER[order], steps_per_graph, grid_ctas, run, tile_w)
         check(self._L.alw_batch_set_tuning(self._h, ctypes.byref(t)))
 
     def tuning(self) -> dict:
@@ -374,7 +381,7 @@ class Batch:
         check(self._L.alw_batch_get_tuning(self._h, ctypes.byref(t)))
         inv = {v: k for k, v in ORDER.items()}
         return {"order": inv.get(t.order, t.order), "steps_per_graph": t.steps_per_graph, "grid_ctas": t.grid_ctas,
-                "run": t.run}
+                "run": t.run, "tile": f"{t.tile_w or 64}x32"}
 
     def build(self):
         """Upload the instances and tune the work list now (run() does it on first use)."""
