@@ -95,3 +95,33 @@ def oracle_stages(case: Case, phi0: np.ndarray, dt: float):
         a_prev = a_own
         cur = nxt
     return outs
+
+
+def oracle_steps(case: Case, phi0: np.ndarray, dt: float, nsteps: int) -> np.ndarray:
+    """nsteps RK3 steps (Step 5) of fixed size dt by the oracle, with the flux alpha as the stage
+    kernels use it and the lagged alpha carried from step to step: a prime pass over phi0, then every
+    stage's grid maximum serves the next stage (local modes use the node's own alpha, fixed the given
+    pair, global exact the stage's own maximum)."""
+    cfg = case.cfg()
+    a_prev, _ = oracle.alpha_of(cfg, phi0)
+    phi = np.array(phi0, dtype=np.float64)
+    for _ in range(nsteps):
+        cur = phi
+        for s in range(3):
+            a_own, _ = oracle.alpha_of(cfg, cur)
+            if case.alpha_mode == "fixed":
+                a_use = np.array(case.alpha_fixed)
+            elif case.alpha_mode == "global_exact":
+                a_use = a_own
+            else:
+                a_use = a_prev
+            Ls = oracle.L_of(cfg, cur, a_use)
+            if s == 0:
+                cur = phi + dt * Ls
+            elif s == 1:
+                cur = 0.75 * phi + 0.25 * (cur + dt * Ls)
+            else:
+                cur = phi / 3.0 + 2.0 * (cur + dt * Ls) / 3.0
+            a_prev = a_own
+        phi = cur
+    return phi

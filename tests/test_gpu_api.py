@@ -100,6 +100,22 @@ def test_non_finite_input_is_reported(precision):
         assert e.value.status == native.ENONFINITE
 
 
+def test_no_progress_is_reported_as_timeout(monkeypatch):
+    # host-side injection: the progress check of alw_step_to sees the device state frozen after its
+    # first read (the device itself keeps working), so the call must give up with ALW_ETIMEOUT
+    # instead of waiting; without the injection the same solver then finishes normally
+    case = Case(2, 64, 48, "burgers2d", precision="mixed", lo=-2.0, hi=2.0)
+    with case.solver() as s:
+        s.set_phi0(case.field(seed=3, kind="smooth"))
+        monkeypatch.setenv("ALW_TEST_FREEZE_STATE_AFTER", "1")
+        with pytest.raises(native.AlwError) as e:
+            s.step_to(0.2)
+        assert e.value.status == native.ETIMEOUT
+        monkeypatch.delenv("ALW_TEST_FREEZE_STATE_AFTER")
+        s.step_to(0.2)
+        assert s.get_state().t == 0.2
+
+
 @pytest.mark.parametrize("precision,alpha", [("mixed", "fixed"), ("mixed", "local_lagged"), ("fp64", "fixed")])
 def test_full_size_8192_sampled_stage_parity(precision, alpha):
     # the bench configuration (Example 3 on 8192^2): one RK stage on the GPU, checked at
@@ -126,6 +142,81 @@ def test_full_size_8192_sampled_stage_parity(precision, alpha):
     err = max(errs) / np.abs(phi0).max()
     tol = 1e-12 if precision == "fp64" else 64 * 2.0**-24
     assert err <= tol, err
+
+
+def _patch_stages(phi0, i, j, dx, dt, alpha, weights):
+    """The oracle's phi_1 on the 13 x 13 nodes, phi_2 on the 7 x 7 nodes and phi^{n+1} at the node
+    around (i, j) of one RK3 step (Step 5) with the flux alpha `alpha` in every stage, from a 19 x 19
+    periodic patch of phi0 centred on (i, j): each stage widens the dependence by three nodes, so
+    the patch's own periodic wrap never reaches a node that is evaluated."""
+    n = phi0.shape[0]
+    rows = (j + np.arange(-9, 10)) % n
+    cols = (i + np.arange(-9, 10)) % n
+    p0 = np.ascontiguousarray(phi0[np.ix_(rows, cols)])
+    cfg = oracle.make_cfg(dim=2, nx=19, ny=19, dx=dx, ham="burgers2d", weights=weights, alpha_mode="global_lagged")
+    p1 = p0.copy()
+    for b in range(3, 16):
+        for a in range(3, 16):
+            p1[b, a] = p0[b, a] + dt * oracle.point_L(cfg, p0, a, b, alpha)
+    p2 = p1.copy()
+    for b in range(6, 13):
+        for a in range(6, 13):
+            p2[b, a] = 0.75 * p0[b, a] + 0.25 * (p1[b, a] + dt * oracle.point_L(cfg, p1, a, b, alpha))
+    p3 = p0[9, 9] / 3.0 + 2.0 * (p2[9, 9] + dt * oracle.point_L(cfg, p2, 9, 9, alpha)) / 3.0
+    return p1, p2, p3
+
+
+@pytest.mark.parametrize("precision,weights", [("mixed", "arclength"), ("mixed", "jp"), ("fp64", "arclength")])
+def test_full_size_8192_three_stages_global_lagged(precision, weights):
+    # The configuration bench.py times (Example 3 on 8192^2, lagged grid-wide alpha): all three RK
+    # stages on the GPU, phi_1, phi_2 and phi^{n+1} checked at sampled nodes -- tile corners and edges,
+    # the periodic seams, random interior nodes -- against the oracle's stages on patches around them.
+    # Flux alpha: the grid maximum of |u + v + 1| over phi0's one-sided derivatives, which the oracle
+    # evaluates on the line x + y = 1 (i + j = 10240), where |phi_x + phi_y + 1| = pi + 1 is attained;
+    # later stages' maxima differ by O(dt) relative, and alpha enters L only through
+    # alpha (u^+ - u^-) / 2, with |u^+ - u^-| = O(dx^5) on these smooth data.
+    n = 8192
+    x, dx = inputs.axis(n, -2.0, 2.0, "periodic")
+    phi0 = np.ascontiguousarray(inputs.phi0_negcos_diag_2d(x, x))
+    cfg = oracle.make_cfg(dim=2, nx=n, ny=n, dx=dx, ham="burgers2d", weights=weights, alpha_mode="global_lagged")
+    amax = 0.0
+    for i in range(2049, 8192, 97):
+        d = oracle.point_derivs(cfg, phi0, i, 10240 - i)
+        amax = max(amax, *(abs(u + v + 1.0) for u in d[:2] for v in d[2:]))
+    assert abs(amax - (1.0 + math.pi)) < 1e-9
+    alpha = np.array([amax, amax])
+    dt = 0.6 / (2 * amax / dx)
+    case = Case(2, n, n, "burgers2d", lo=-2.0, hi=2.0, precision=precision, weights=weights,
+                alpha_mode="global_lagged")
+    with case.solver() as s:
+        s.set_phi0(phi0)
+        s.run_stage(1, dt)
+        g1 = s.get_stage_phi(1)
+        s.run_stage(2, dt)
+        g2 = s.get_stage_phi(2)
+        s.run_stage(3, dt)
+        g3 = s.get_phi()
+        a_gpu = s.get_state().alpha
+    rng = np.random.default_rng(81920)
+    pts = [(0, 0), (n - 1, n - 1), (0, n - 1), (n - 1, 0), (63, 31), (64, 32), (8191, 4095), (4096, 8191),
+           (2, 5000), (8189, 17), (3000, 8190), (1000, 2)]
+    pts += [(int(i), int(j)) for i, j in rng.integers(0, n, size=(60, 2))]
+    tol = (1e-12 if precision == "fp64" else 64 * 2.0**-24) * np.abs(phi0).max()
+    errs = [0.0, 0.0, 0.0]
+    for i, j in pts:
+        p1, p2, p3 = _patch_stages(phi0, i, j, dx, dt, alpha, weights)
+        rows = (j + np.arange(-6, 7)) % n
+        cols = (i + np.arange(-6, 7)) % n
+        errs[0] = max(errs[0], np.abs(g1[np.ix_(rows, cols)] - p1[3:16, 3:16]).max())
+        rows, cols = (j + np.arange(-3, 4)) % n, (i + np.arange(-3, 4)) % n
+        errs[1] = max(errs[1], np.abs(g2[np.ix_(rows, cols)] - p2[6:13, 6:13]).max())
+        errs[2] = max(errs[2], abs(g3[j, i] - p3))
+    assert max(errs) <= tol, (errs, tol)
+    # the lagged alpha the GPU holds after stage 3 is the grid maximum over phi_2's derivatives: the
+    # gradient is constant along characteristics, so it differs from phi0's maximum only by where the
+    # nodes sample the moved profile, O(dt^2) relative, and never exceeds pi + 1 beyond rounding
+    for a in a_gpu:
+        assert abs(a - amax) <= 1e-5 * amax and a <= (1.0 + math.pi) * (1 + 1e-6), (a, amax)
 
 
 @pytest.mark.parametrize("weights", ["arclength", "jp"])

@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 from paper_1909_13263_gb300 import inputs, native
+from test_gpu_batch import MIXED_SOLVE_TOL, oracle_solve
 
 pytestmark = pytest.mark.gpu
 
@@ -68,3 +69,28 @@ def test_server_limits():
     with pytest.raises(native.AlwError) as e:
         native.Server(hbm_budget_bytes=1 << 20, max_slots=2, max_side=1024)
     assert e.value.status == native.EBUDGET
+
+
+def test_served_results_match_oracle():
+    # requests of uneven size and both Hamiltonians, submitted while others are resident: each
+    # result against the oracle's solve of that request alone
+    insts = [inputs.Instance(i.n, i.ham, i.theta, i.t_final * 0.3)
+             for i in inputs.batch_instances(8, 24, 200, seed=91)]
+    insts.append(inputs.Instance(65, "burgers2d" if insts[0].ham == "negcos2d" else "negcos2d", 1.3,
+                                 0.1 / math.pi**2))
+    assert {i.ham for i in insts} == {"burgers2d", "negcos2d"}
+    with native.Server(hbm_budget_bytes=1 << 30, max_slots=4, max_side=256) as srv:
+        srv.set_round_steps(2)
+        ids = []
+        for k, inst in enumerate(insts):
+            phi0, _ = inputs.instance_phi0(inst)
+            ids.append(srv.submit(nx=inst.n, ny=inst.n, xlo=-2.0, xhi=2.0, ylo=-2.0, yhi=2.0, ham=inst.ham,
+                                  phi0=phi0, t_final=inst.t_final))
+            if k % 3 == 2:
+                time.sleep(0.005)
+        results = [srv.poll(rid, timeout=120.0) for rid in ids]
+    for inst, (done, info, out) in zip(insts, results):
+        assert done and info["status"] == 0
+        ref, _ = oracle_solve(inst, "arclength")
+        err = float(np.max(np.abs(out - ref)))
+        assert err <= MIXED_SOLVE_TOL, (inst, err)
