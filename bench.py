@@ -44,8 +44,10 @@ FP32_LANES_PER_SM = 128
 # per direction 3 F evaluations (rsqrt + lg2), 3 interval means (1 reciprocal each),
 # 2 weight sets (1 reciprocal each) -> 11 MUFU ops; FP32 flops ~107 per direction
 # plus ~33 for alpha, H-hat and the RK combination; bytes: each array read or written once per stage
+# (MIXED arc length on smooth data runs the short-interval sweep: per direction 3 square roots and
+# 2 weight reciprocals, 5 MUFU ops; "mufu_full" is the count of the full sweep)
 ALGO = {
-    ("arclength", "mixed"): {"mufu": 22, "flops": 250, "bytes": (12, 16, 20)},
+    ("arclength", "mixed"): {"mufu": 10, "mufu_full": 22, "flops": 250, "bytes": (12, 16, 20)},
     ("arclength", "fp32"): {"mufu": 22, "flops": 240, "bytes": (8, 12, 12)},
     ("jp", "mixed"): {"mufu": 4, "flops": 180, "bytes": (12, 16, 20)},
     ("jp", "fp32"): {"mufu": 4, "flops": 170, "bytes": (8, 12, 12)},
@@ -271,8 +273,9 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"ex3_burgers2d_{args.n}sq",
-                   "sample": f"{cores} independent {n}x{n} grids (one per core), 1 RK3 step each per bench step",
+        "config": {"workload": f"ex3_burgers2d_{args.n}sq", "sample_grid": f"{n}x{n}",
+                   "sample": f"each bench step: one RK3 step of the workload's scheme on {cores} independent "
+                             f"{n}x{n} grids (one per core), not on the {args.n}x{args.n} grid itself",
                    "weights": "arclength"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"one RK3 step of Example 3 on {cores} independent {n}x{n} grids "
@@ -311,6 +314,19 @@ def bench_batched(args, stream):
         tuning = b.tuning()
         mem = b.memory_bytes()
     t_batch = time.perf_counter() - t0
+    # each tile width the autotuner chooses from, fixed, on the same batch (host to host, as above)
+    widths = {}
+    for w in (64, 32):
+        t1 = time.perf_counter()
+        with native.Batch(precision="mixed", weights=args.weights, stream=stream) as bw:
+            for inst, ph in zip(insts, phis):
+                bw.add(nx=inst.n, ny=inst.n, ham=inst.ham, phi0=ph, t_final=inst.t_final, **kw)
+            bw.set_tuning(order=tuning["order"], steps_per_graph=tuning["steps_per_graph"], run=tuning["run"],
+                          tile_w=w)
+            bw.run()
+            for k in range(len(insts)):
+                bw.get_phi(k)
+        widths[f"{w}x32"] = {"solves_per_s": len(insts) / (time.perf_counter() - t1)}
     serial_n = min(len(insts), args.serial_count)
     t0 = time.perf_counter()
     for inst, ph in list(zip(insts, phis))[:serial_n]:
@@ -324,7 +340,8 @@ def bench_batched(args, stream):
     return {"instances": len(insts), "solves_per_s": len(insts) / t_batch,
             "serial_solves_per_s": serial_n / t_serial, "speedup_vs_serial": (len(insts) / t_batch) / (serial_n / t_serial),
             "point_updates_per_s": node_steps / t_batch, "wall_s": t_batch, "graph_replays": replays,
-            "tuning": tuning, "device_bytes": mem, "serial_sample": serial_n, "finite": ok}
+            "tuning": tuning, "tile_widths_fixed": widths, "device_bytes": mem, "serial_sample": serial_n,
+            "finite": ok}
 
 
 def bench_serving(args, stream, rate):
@@ -494,6 +511,80 @@ def run_sizes_report(args):
     return 0
 
 
+def bench_precision(args, stream):
+    """Errors of the MIXED path (the timed precision) against FP64 and the exact solution.
+
+    Example 10 (sin(p + q), pi(|y| - |x|), linear extrapolation; no closed-form solution) on 1024^2 to
+    t = 1: MIXED against the FP64 path, max |e| and mean |e|.  Example 3 on 2048^2 to t = 0.5/pi^2:
+    FP64 and MIXED against the exact solution (characteristics) and MIXED against FP64."""
+    import numpy as np
+
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import exact
+    from paper_1909_13263_gb300 import inputs, native
+
+    out = {"norms": "max = max |e|, l1 = mean |e| over the nodes"}
+    n = args.precision_ex10_n
+    x, _ = inputs.axis(n, -1.0, 1.0, "linextrap")
+    phi0 = inputs.phi0_riemann_2d(x, x)
+    res = {}
+    for prec in ("fp64", "mixed"):
+        with native.Solver(dim=2, nx=n, ny=n, bc="linextrap", xlo=-1.0, xhi=1.0, ylo=-1.0, yhi=1.0,
+                           ham="sin2d", precision=prec, stream=stream) as s:
+            s.set_phi0(phi0)
+            steps = s.step_to(1.0)
+            res[prec] = s.get_phi()
+    d = np.abs(res["mixed"] - res["fp64"])
+    out[f"ex10_sin2d_linextrap_{n}sq_t1"] = {"steps": steps, "mixed_vs_fp64_max": float(d.max()),
+                                             "mixed_vs_fp64_l1": float(d.mean())}
+    n = args.precision_ex3_n
+    x, _ = inputs.axis(n, -2.0, 2.0, "periodic")
+    tf = 0.5 / math.pi**2
+    ex = exact.negcos_diag_2d("burgers2d", x, x, tf)
+    res = {}
+    for prec in ("fp64", "mixed"):
+        with native.Solver(dim=2, nx=n, ny=n, xlo=-2.0, xhi=2.0, ylo=-2.0, yhi=2.0, ham="burgers2d",
+                           precision=prec, stream=stream) as s:
+            s.set_phi0(inputs.phi0_negcos_diag_2d(x, x))
+            s.step_to(tf)
+            res[prec] = s.get_phi()
+    row = {}
+    for prec, phi in res.items():
+        e = np.abs(phi - ex)
+        row[f"{prec}_vs_exact_max"] = float(e.max())
+        row[f"{prec}_vs_exact_l1"] = float(e.mean())
+    d = np.abs(res["mixed"] - res["fp64"])
+    row["mixed_vs_fp64_max"] = float(d.max())
+    row["mixed_vs_fp64_l1"] = float(d.mean())
+    row["mixed_l1_ratio_to_fp64"] = row["mixed_vs_exact_l1"] / row["fp64_vs_exact_l1"]
+    out[f"ex3_burgers2d_{n}sq"] = row
+    return out
+
+
+def bench_fp64(args, stream):
+    """The FP64 path (the oracle-parity precision) on the bench grid: RK3 steps timed with CUDA events."""
+    import torch
+
+    from paper_1909_13263_gb300 import inputs, native
+
+    n = args.n
+    x, _ = inputs.axis(n, -2.0, 2.0, "periodic")
+    with native.Solver(dim=2, nx=n, ny=n, xlo=-2.0, xhi=2.0, ylo=-2.0, yhi=2.0, ham="burgers2d",
+                       precision="fp64", weights=args.weights, alpha_mode="global_lagged", stream=stream) as s:
+        s.set_phi0(inputs.phi0_negcos_diag_2d(x, x))
+        s.advance(3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.advance(args.fp64_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.fp64_steps
+    return {"workload": f"ex3_burgers2d_{n}sq", "value": n * n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "steps": args.fp64_steps, "bound": "fp64 pipe",
+            "fp64_pipe_note": "ncu: FP64 pipe 86 % busy on this kernel (profiles/stage_kernel_fp64_ex3_arclength_1024.md)"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -533,7 +624,8 @@ def run_ours(args):
         s.sync()
         ms = ev0.elapsed_time(ev1)
         clocks = cs.summary()
-        # per-stage device time of the stage kernel (events on the launching stream)
+        # per-stage device time of the stage kernel, each stage launched alone (events on the launching
+        # stream): a breakdown only -- the roofline uses the launches inside the timed graph replays
         st = s.get_state()
         dt = 0.6 / (st.alpha[0] / dx + st.alpha[1] / dx)
         reps = 5
@@ -576,43 +668,63 @@ def run_ours(args):
             batched = bench_batched(args, stream)
     if not args.no_serve:
         with torch.cuda.stream(stream):
-            rates = [float(r) for r in args.serve_rates.split(",")] if args.serve_rates else [args.serve_rate]
+            rates = [float(r) for r in args.serve_rates.split(",") if r]
             runs = [bench_serving(args, stream, r) for r in rates]
-            serving = runs[0] if len(runs) == 1 else {"sweep": runs}
+            top = max(runs, key=lambda r: r["served"]["rate_per_s"])
+            serving = {"sweep": runs, "rates_per_s": rates,
+                       "solves_per_s_vs_serial_at_highest_rate": top["solves_per_s_vs_serial"],
+                       "p99_not_above_serial_at_every_rate": all(r["served"]["p99_s"] <= r["serial"]["p99_s"]
+                                                                 for r in runs)}
+    precision = fp64 = None
+    if not args.no_precision:
+        with torch.cuda.stream(stream):
+            precision = bench_precision(args, stream)
+    if not args.no_fp64:
+        with torch.cuda.stream(stream):
+            fp64 = bench_fp64(args, stream)
 
     if rank != 0:
         return 0
     peaks, src = _peaks()
     algo = ALGO.get((args.weights, args.precision), ALGO[("arclength", "mixed")])
     pts = n * n
-    stage_total_ms = sum(stage_ms)
-    mufu_achieved = algo["mufu"] * pts * 3 / (stage_total_ms * 1e-3) / 1e9        # Gop/s
+    # the dominant kernel's average launch duration inside the timed region: a periodic grid's RK3 step
+    # graph holds exactly the three stage launches (no ghost or reduction kernels), so the per-launch
+    # average is the graph-timed step time / 3 (graph gaps included: achieved is, if anything, low)
+    launch_ms = ms / (3 * args.steps)
+    bytes_launch = sum(algo["bytes"]) * pts / 3.0       # algorithmic bytes of an average stage launch
+    hbm_achieved = bytes_launch / (launch_ms * 1e-3) / 1e9
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    mufu_achieved = algo["mufu"] * pts / (launch_ms * 1e-3) / 1e9        # Gop/s
     mufu_peak = SM_COUNT * MUFU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e9
-    bytes_step = sum(algo["bytes"]) * pts
-    hbm_achieved = bytes_step / (stage_total_ms * 1e-3) / 1e9
     traffic = _traffic()
     roof = {
-        "kernel": "stage_kernel (3 launches per RK3 step; per-launch average)",
-        "bound": "alu",
-        "unit": "Gop/s",
-        "achieved": mufu_achieved,
-        "peak": mufu_peak,
-        "frac": mufu_achieved / mufu_peak,
-        "peak_source": f"derived: {SM_COUNT} SMs x {MUFU_PER_SM_CLK} MUFU/clk x {SM_MAX_MHZ:.0f} MHz",
+        "kernel": "stage2d_kernel (3 launches per RK3 step; per-launch average over the timed graph replays)",
+        "bound": "hbm",
+        "unit": "GB/s",
+        "achieved": hbm_achieved,
+        "peak": hbm_peak,
+        "frac": hbm_achieved / hbm_peak,
+        "peak_source": f"{src}: MEASURED_PEAKS.json hbm_gbs (copy bandwidth)" if src == "measured" else src,
+        "algorithmic_bytes_per_launch": bytes_launch,
+        "algorithmic_bytes_per_point_step": sum(algo["bytes"]),
+        "launch_ms": launch_ms,
         "traffic": (traffic["dram_bytes_per_point_step"] * pts / 3.0) if traffic else None,
-        "stage_ms": stage_ms,
-        "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": peaks.get("hbm_gbs"),
-                "frac": hbm_achieved / peaks.get("hbm_gbs", 6800.0), "peak_source": src,
-                "algorithmic_bytes_per_point_step": sum(algo["bytes"])},
-        "fp32": {"achieved_tflops": algo["flops"] * pts * 3 / (stage_total_ms * 1e-3) / 1e12,
+        "traffic_source": traffic.get("measured_on") if traffic else "no capture of the current kernel",
+        "stage_ms_isolated": stage_ms,
+        "alu": {"unit": "Gop/s", "achieved": mufu_achieved, "peak": mufu_peak, "frac": mufu_achieved / mufu_peak,
+                "mufu_per_point_stage": algo["mufu"], "mufu_per_point_stage_full_sweep": algo.get("mufu_full"),
+                "peak_source": f"measured 16 MUFU ops/SM/clk (rsqrt, sqrt, lg2, sin) x {SM_COUNT} SMs x "
+                               f"{SM_MAX_MHZ:.0f} MHz"},
+        "fp32": {"achieved_tflops": algo["flops"] * pts / (launch_ms * 1e-3) / 1e12,
                  "peak_tflops": SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12},
     }
-    # instruction issue, the unit this kernel saturates: thread instructions per node and stage from the
-    # same ncu capture as the traffic (arc length, MIXED) against 4 schedulers x 32 lanes per SM and clock
+    # instruction issue: thread instructions per node and stage from the same ncu capture as the traffic
+    # (arc length, MIXED) against 4 schedulers x 32 lanes per SM and clock
     if traffic and traffic.get("thread_instructions_per_point_stage") and \
             (args.weights, args.precision) == ("arclength", "mixed"):
         inst = traffic["thread_instructions_per_point_stage"]
-        achieved = sum(inst) * pts / (stage_total_ms * 1e-3) / 1e12
+        achieved = sum(inst) / 3.0 * pts / (launch_ms * 1e-3) / 1e12
         peak = SM_COUNT * 4 * 32 * SM_MAX_MHZ * 1e6 / 1e12
         roof["issue"] = {"achieved_tinst_s": achieved, "peak_tinst_s": peak, "frac": achieved / peak,
                          "peak_source": f"derived: {SM_COUNT} SMs x 4 schedulers x 32 lanes x {SM_MAX_MHZ:.0f} MHz",
@@ -647,6 +759,8 @@ def run_ours(args):
         "clocks": clocks,
         "batched": batched,
         "serving": serving,
+        "precision": precision,
+        "fp64": fp64,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:
@@ -750,11 +864,16 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--serial-count", type=int, default=128)
-    ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--precision-ex10-n", type=int, default=1024)
+    ap.add_argument("--precision-ex3-n", type=int, default=2048)
+    ap.add_argument("--fp64-steps", type=int, default=4)
+    ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--serve-round-steps", type=int, default=4)
     ap.add_argument("--serve-round-tiles", type=int, default=None,
                     help="tile limit of a server round (default: the server's own, four kernel waves; 0: none)")
-    ap.add_argument("--serve-rates", type=str, default="", help="comma-separated arrival rates (a sweep)")
+    ap.add_argument("--serve-rates", type=str, default="50,200,1000,2000",
+                    help="comma-separated Poisson arrival rates of the serving sweep (req/s)")
     ap.add_argument("--report", choices=["", "precision", "sizes", "oracle"], default="",
                     help="precision: errors of the float paths against FP64 and the exact solution; sizes: "
                          "device throughput by grid size; oracle: the FP64 CPU oracle timed on the host cores")
@@ -762,7 +881,7 @@ def main():
                     help="precision report: grid sides of Example 3 (comma-separated)")
     ap.add_argument("--report-ex10-sizes", type=str, default="1024",
                     help="precision report: grid sides of Example 10 (comma-separated)")
-    ap.add_argument("--serve-count", type=int, default=120)
+    ap.add_argument("--serve-count", type=int, default=200)
     ap.add_argument("--serve-budget-gb", type=float, default=60.0)
     args = ap.parse_args()
     if args.warmup < 3:
