@@ -22,16 +22,20 @@
 //   omega_0 = A0 / den, omega_2 = 3 A2 / den,
 //   phi^- = (c + T_b/12) - (A0 T_a / 3 + A2 T_b / 2) / den,
 //   phi^+ = (c - T_b/12) + (A0' T_c / 3 + A2' T_b / 2) / den'.
+// The central parts are formed from d_m = s_{m+1} - s_m (s_m = v_m - v_{m-1}): for the node between
+// v_2 and v_3 of its window, c + T_b/12 = (v_2 + v_3)/2 - d_2/6 and c - T_b/12 = (v_2 + v_3)/2 - d_3/6,
+// and T_m = d_m - d_{m-1}; the widths d_m / dx are those of the arc-length intervals.
 //
 // Short intervals.  The interval mean G takes the trapezoid value (s_a + s_b) / 2 whenever the
 // interval [a, b] is short against its end values (|b - a| <= (s_a + s_b) / 64, s = sqrt(1 + u^2)).
 // On smooth data at fine grids every interval of a segment is that short (its width is a third
 // difference of phi over dx^2, about phi_xxx dx), and then F, its logarithm and the interval
 // reciprocals are never used.  sweep_stream_short computes only what the trapezoid branch needs
-// and reports whether the segment qualifies: every width D2_{m+1} - D2_m of the segment at most
-// kShortH (which implies the trapezoid branch for all three interval kinds, because
-// R_m - D2_m = D2_m - D2_{m-1} and D2_m - L_m = D2_{m+1} - D2_m up to one rounding of R or L,
-// and s >= 1), |D2| at the segment start at most kShortD2 and eps4 at most kShortEps4 (together
+// and reports whether the segment qualifies: every width W_m = d_m / dx of the segment at most
+// kShortH (which implies the trapezoid branch for all three interval kinds, because D2_{m+1} - D2_m,
+// R_m - D2_m and D2_m - L_m all equal such a width up to the rounding of D2, R or L -- below 1e-4
+// while |D2| <= kShortD2, against the margin 1/32 - kShortH -- and s >= 1), |D2| at the segment
+// start at most kShortD2 and eps4 at most kShortEps4 (together
 // these keep every weight denominator below 1e29, so the overflow branch of side_corr_v cannot be
 // taken).  When the segment qualifies, both sweeps evaluate the same formulas on the same branches;
 // their results agree to rounding (the compiler may select instructions for the two code paths
@@ -249,35 +253,40 @@ __device__ __forceinline__ bool short_sizes(V d2, V eps4) {
 }
 
 // The extrapolated interval ends R_m = 2 D2_m - D2_{m-1} and L_m = 2 D2_m - D2_{m+1}, formed as
-// D2_m plus or minus the neighbouring width (the widths are the quantities the short-interval test
+// D2_m plus or minus the neighbouring width W = d / dx (the quantity the short-interval test
 // inspects; one operation each).
 template <class V>
-__device__ __forceinline__ V r_end(V d2m, V d2prev) { return vadd(d2m, vsub(d2m, d2prev)); }
+__device__ __forceinline__ V r_end(V d2m, V w_prev) { return vadd(d2m, w_prev); }
 template <class V>
-__device__ __forceinline__ V l_end(V d2m, V d2next) { return vsub(d2m, vsub(d2next, d2m)); }
+__device__ __forceinline__ V l_end(V d2m, V w_m) { return vsub(d2m, w_m); }
 
 template <int K, int WEIGHTS, class V, class LoadV, class Emit>
 __device__ __forceinline__ void sweep_stream(LoadV v_at, V rdx, V eps4, V eps, Emit emit) {
   V v[K + 5];
   V s[K + 5];
+  V dd[K + 5];                               // d_m = s_{m+1} - s_m
   V T[K + 5];
   V qX[K + 6], qY[K + 6], qZ[K + 6];
   V D2[K + 6];
+  V W[K + 6];                                // W_m = d_m / dx = D2_{m+1} - D2_m up to rounding
   FValV<V> FD[K + 6];
-  const V mtwo = vsplat(-2.0f, eps);
 
-  auto pos_s = [&](int m) {                  // s, and D2 for arc length
+  auto pos_s = [&](int m) {                  // s, d, and D2 and W for arc length
     s[m] = vsub(v[m], v[m - 1]);
     if (WEIGHTS == W_ARCLEN) D2[m] = vmul(s[m], rdx);
+    if (m >= 2) {
+      dd[m - 1] = vsub(s[m], s[m - 1]);
+      if (WEIGHTS == W_ARCLEN) W[m - 1] = vmul(dd[m - 1], rdx);
+    }
   };
-  auto pos_T = [&](int m) { T[m] = vfma(mtwo, s[m], vadd(s[m - 1], s[m + 1])); };
+  auto pos_T = [&](int m) { T[m] = vsub(dd[m], dd[m - 1]); };
   auto al_qX = [&](int m) {                  // interval (D2_m, R_m), R = 2 D2_m - D2_{m-1}
-    const V R = r_end(D2[m], D2[m - 1]);
+    const V R = r_end(D2[m], W[m - 1]);
     qX[m] = q_interval_v(D2[m], FD[m], R, f_eval_v(R), eps4);
   };
   auto al_qY = [&](int m) { qY[m] = q_interval_v(D2[m], FD[m], D2[m + 1], FD[m + 1], eps4); };
   auto al_qZ = [&](int m) {                  // interval (L_m, D2_m), L = 2 D2_m - D2_{m+1}
-    const V Lv = l_end(D2[m], D2[m + 1]);
+    const V Lv = l_end(D2[m], W[m]);
     qZ[m] = q_interval_v(Lv, f_eval_v(Lv), D2[m], FD[m], eps4);
   };
   auto jp_pair = [&](int m) {                // Jiang-Peng quantities of the pair (s_m, s_{m+1})
@@ -310,13 +319,13 @@ __device__ __forceinline__ void sweep_stream(LoadV v_at, V rdx, V eps4, V eps, E
     for (int m = 1; m <= 4; ++m) jp_pair(m);
   }
 
-  const V c712 = vsplat(7.0f / 12.0f, eps), cm112 = vsplat(-1.0f / 12.0f, eps), c112 = vsplat(1.0f / 12.0f, eps);
+  const V cm16 = vsplat(-1.0f / 6.0f, eps);
   const V c13 = vsplat(1.0f / 3.0f, eps), cm13 = vsplat(-1.0f / 3.0f, eps);
   const V c12 = vsplat(0.5f, eps), cm12 = vsplat(-0.5f, eps);
 #pragma unroll
   for (int p = 0; p < K; ++p) {
     // node p: phi^- = (c + T_b/12) - corr^-, phi^+ = (c - T_b/12) + corr^+
-    const V c = vfma(c712, vadd(v[p + 2], v[p + 3]), vmul(cm112, vadd(v[p + 1], v[p + 4])));
+    const V mid = vmul(c12, vadd(v[p + 2], v[p + 3]));
     const V tb = T[p + 3];
     V nm, rm, np, rp;
     if (WEIGHTS == W_ARCLEN) {
@@ -326,7 +335,7 @@ __device__ __forceinline__ void sweep_stream(LoadV v_at, V rdx, V eps4, V eps, E
       side_corr_v(qX[p + 1], qY[p + 2], qZ[p + 3], vmul(T[p + 2], cm13), vmul(cm12, tb), nm, rm);
       side_corr_v(qZ[p + 4], qY[p + 3], qX[p + 2], vmul(T[p + 4], c13), vmul(c12, tb), np, rp);
     }
-    emit(p, vfma(nm, rm, vfma(tb, c112, c)), vfma(np, rp, vfma(tb, cm112, c)));
+    emit(p, vfma(nm, rm, vfma(dd[p + 2], cm16, mid)), vfma(np, rp, vfma(dd[p + 3], cm16, mid)));
     // advance the window by one position
     if (p + 1 < K) {
       v[p + 6] = v_at(p + 6);
@@ -356,11 +365,12 @@ __device__ __forceinline__ bool sweep_stream_short(LoadV v_at, V rdx, V eps4, Em
   using LN = Lanes<V>;
   V v[K + 5];
   V s[K + 5];
+  V dd[K + 5];
   V T[K + 5];
   V D2[K + 6];
+  V W[K + 6];
   V S[K + 6];                                // S_m = sqrt(1 + D2_m^2)
   V qX[K + 6], qY[K + 6], qZ[K + 6];
-  const V mtwo = vsplat(-2.0f, rdx);
   bool ok = true;
 
   auto sq = [&](V u) { return s_eval_v(u); };   // FValV::s of f_eval_v
@@ -372,12 +382,16 @@ __device__ __forceinline__ bool sweep_stream_short(LoadV v_at, V rdx, V eps4, Em
   auto pos_s = [&](int m) {
     s[m] = vsub(v[m], v[m - 1]);
     D2[m] = vmul(s[m], rdx);
-    if (m >= 2) ok &= short_width(vsub(D2[m], D2[m - 1]));
+    if (m >= 2) {
+      dd[m - 1] = vsub(s[m], s[m - 1]);
+      W[m - 1] = vmul(dd[m - 1], rdx);
+      ok &= short_width(W[m - 1]);
+    }
   };
-  auto pos_T = [&](int m) { T[m] = vfma(mtwo, s[m], vadd(s[m - 1], s[m + 1])); };
-  auto al_qX = [&](int m) { qX[m] = qv(S[m], sq(r_end(D2[m], D2[m - 1]))); };
+  auto pos_T = [&](int m) { T[m] = vsub(dd[m], dd[m - 1]); };
+  auto al_qX = [&](int m) { qX[m] = qv(S[m], sq(r_end(D2[m], W[m - 1]))); };
   auto al_qY = [&](int m) { qY[m] = qv(S[m], S[m + 1]); };
-  auto al_qZ = [&](int m) { qZ[m] = qv(sq(l_end(D2[m], D2[m + 1])), S[m]); };
+  auto al_qZ = [&](int m) { qZ[m] = qv(sq(l_end(D2[m], W[m])), S[m]); };
   // side_corr_v when the denominator is known to be in range
   auto corr = [&](V q0, V q1, V q2, V ta3, V tb2, V &num, V &rd) {
     const V A0 = vmul(q1, q2), A1 = vmul(q0, q2), A2 = vmul(q0, q1);
@@ -400,17 +414,17 @@ __device__ __forceinline__ bool sweep_stream_short(LoadV v_at, V rdx, V eps4, Em
   ok &= short_sizes(D2[2], eps4);
   if (!__all_sync(0xffffffffu, ok)) return false;
 
-  const V c712 = vsplat(7.0f / 12.0f, rdx), cm112 = vsplat(-1.0f / 12.0f, rdx), c112 = vsplat(1.0f / 12.0f, rdx);
+  const V cm16 = vsplat(-1.0f / 6.0f, rdx);
   const V c13 = vsplat(1.0f / 3.0f, rdx), cm13 = vsplat(-1.0f / 3.0f, rdx);
   const V c12 = vsplat(0.5f, rdx), cm12 = vsplat(-0.5f, rdx);
 #pragma unroll
   for (int p = 0; p < K; ++p) {
-    const V c = vfma(c712, vadd(v[p + 2], v[p + 3]), vmul(cm112, vadd(v[p + 1], v[p + 4])));
+    const V mid = vmul(c12, vadd(v[p + 2], v[p + 3]));
     const V tb = T[p + 3];
     V nm, rm, np, rp;
     corr(qX[p + 2], qY[p + 2], qZ[p + 3], vmul(T[p + 2], cm13), vmul(cm12, tb), nm, rm);
     corr(qZ[p + 4], qY[p + 3], qX[p + 3], vmul(T[p + 4], c13), vmul(c12, tb), np, rp);
-    emit(p, vfma(nm, rm, vfma(tb, c112, c)), vfma(np, rp, vfma(tb, cm112, c)));
+    emit(p, vfma(nm, rm, vfma(dd[p + 2], cm16, mid)), vfma(np, rp, vfma(dd[p + 3], cm16, mid)));
     if (p + 1 < K) {
       v[p + 6] = v_at(p + 6);
       pos_s(p + 6);
