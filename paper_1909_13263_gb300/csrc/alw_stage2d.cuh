@@ -49,9 +49,11 @@ template <> struct Ham2<H_BURGERS2D> {
   }
   __device__ __forceinline__ static void alpha(float um, float up, float vm, float vp, float, float, float &ax,
                                                     float &ay) {
-    // |H_p| = |H_q| = |u + v + 1| at the four corners (u + 1 shared by two of them)
-    const float u0 = um + 1.0f, u1 = up + 1.0f;
-    ax = ay = fmaxf(fmaxf(fabsf(u0 + vm), fabsf(u0 + vp)), fmaxf(fabsf(u1 + vm), fabsf(u1 + vp)));
+    // |H_p| = |H_q| = |u + v + 1| at the four corners: the largest and the smallest corner sums are
+    // max(u) + 1 + max(v) and min(u) + 1 + min(v), and |.| is largest at one of them (the same
+    // values as the four corner sums, with the comparisons on the integer/logic pipe)
+    const float hi = (fmaxf(um, up) + 1.0f) + fmaxf(vm, vp), lo = (fminf(um, up) + 1.0f) + fminf(vm, vp);
+    ax = ay = fmaxf(fabsf(hi), fabsf(lo));
   }
 };
 template <> struct Ham2<H_NEGCOS2D> {
@@ -358,14 +360,10 @@ __global__ void __launch_bounds__(Geo2D<TXv>::NT, Geo2D<TXv>::MINB)
       __syncthreads();
       continue;
     }
+    // every thread waits for the tile's loads itself; no CTA barrier here: the buffers, the tile
+    // records and the phi_x hand-off of the previous tile are rewritten only after the barrier that
+    // follows the differences pass, which every thread reaches after finishing the previous tile
     const bool ok = mbar_wait_bounded(&bars[buf], (phase >> buf) & 1u);
-    if (__syncthreads_or(!ok)) {
-      // a tile load never completed: flag the instance and stop (the next tile's load is issued
-      // only after this wait, so no other load is in flight)
-      if (tid == 0) atomicOr(&s_info[buf].st->err, 2);
-      __syncthreads();
-      return;
-    }
     phase ^= 1u << buf;
 
     const TileInfo &d = s_info[buf];  // this tile's instance fields (shared memory)
@@ -409,7 +407,14 @@ __global__ void __launch_bounds__(Geo2D<TXv>::NT, Geo2D<TXv>::MINB)
     };
     if (has_delta) diff_pass(std::true_type{});
     else diff_pass(std::false_type{});
-    __syncthreads();
+    if (__syncthreads_or(!ok)) {
+      // a tile load never completed (the differences pass above ran on whatever the buffer held):
+      // flag the instance and stop; the next tile's load is issued only after this barrier, so no
+      // other load is in flight
+      if (tid == 0) atomicOr(&s_info[buf].st->err, 2);
+      __syncthreads();
+      return;
+    }
     // every thread has finished the previous tile (its finish loop read buffer buf ^ 1), so the next
     // tile's load can go there; the barrier after the sweeps publishes s_info[buf ^ 1]
     prepare_next(next, buf);
@@ -549,8 +554,9 @@ __global__ void __launch_bounds__(Geo2D<TXv>::NT, Geo2D<TXv>::MINB)
     const bool more = next < ntiles;
     if (more && !s_info[buf ^ 1].skip && s_info[buf ^ 1].inst == i_inst) {
       // no barrier: the next tile's differences pass writes only dX, which this tile read
-      // before the barrier after the sweeps; su and raw[buf] are rewritten only after the next
-      // tile's first barrier, which every thread reaches after finishing this tile
+      // before the barrier after the sweeps; su, raw[buf] and s_info[buf] are rewritten only
+      // after the next tile's barrier that follows its differences pass, which every thread
+      // reaches after finishing this tile
       continue;
     }
     if (HamSel<H>::kSameAlpha) amy = amx;

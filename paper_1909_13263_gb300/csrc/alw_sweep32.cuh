@@ -195,9 +195,10 @@ static __device__ __noinline__ float side_corr_wide(float q0, float q1, float q2
 
 // The side's correction (A0 T_a / 3 + A2 T_b / 2) / den as a pair (num, r) with correction =
 // num * r (r = 1 / den; on the rare lanes whose products leave the float range, num = the
-// correction and r = 1); ta3 = T_a / 3, tb2 = T_b / 2 (both negated for the "-" side, whose
-// correction is subtracted).  The caller adds it to the central part with one fused multiply-add.
-template <class V>
+// correction and r = 1); ta3 = T_a / 3, tb2 = T_b / 2.  NEG (the "-" side, whose correction is
+// subtracted) gives r = -1 / den (or -1), so that the caller adds num * r to the central part with
+// one fused multiply-add on either side.
+template <bool NEG, class V>
 __device__ __forceinline__ void side_corr_v(V q0, V q1, V q2, V ta3, V tb2, V &num_out, V &r_out) {
   using LN = Lanes<V>;
   const V A0 = vmul(q1, q2), A1 = vmul(q0, q2), A2 = vmul(q0, q1);
@@ -211,7 +212,7 @@ __device__ __forceinline__ void side_corr_v(V q0, V q1, V q2, V ta3, V tb2, V &n
   for (int i = 0; i < LN::n; ++i) {
     const float dn = LN::get(den, i);
     ok = ok && (dn < 1e30f);
-    LN::at(rd, i) = sfu_rcp(dn);
+    LN::at(rd, i) = sfu_rcp(NEG ? -dn : dn);
   }
   V nm = num;
   if (!ok) {
@@ -221,7 +222,7 @@ __device__ __forceinline__ void side_corr_v(V q0, V q1, V q2, V ta3, V tb2, V &n
       if (!(dn < 1e30f)) {
         LN::at(nm, i) = side_corr_wide(LN::get(q0, i), LN::get(q1, i), LN::get(q2, i), LN::get(ta3, i),
                                        LN::get(tb2, i));
-        LN::at(rd, i) = 1.0f;
+        LN::at(rd, i) = NEG ? -1.0f : 1.0f;
       }
     }
   }
@@ -266,6 +267,7 @@ __device__ __forceinline__ void sweep_stream(LoadV v_at, V rdx, V eps4, V eps, E
   V s[K + 5];
   V dd[K + 5];                               // d_m = s_{m+1} - s_m
   V T[K + 5];
+  V T3[K + 5];                               // T_m / 3
   V qX[K + 6], qY[K + 6], qZ[K + 6];
   V D2[K + 6];
   V W[K + 6];                                // W_m = d_m / dx = D2_{m+1} - D2_m up to rounding
@@ -279,7 +281,11 @@ __device__ __forceinline__ void sweep_stream(LoadV v_at, V rdx, V eps4, V eps, E
       if (WEIGHTS == W_ARCLEN) W[m - 1] = vmul(dd[m - 1], rdx);
     }
   };
-  auto pos_T = [&](int m) { T[m] = vsub(dd[m], dd[m - 1]); };
+  const V c13 = vsplat(1.0f / 3.0f, eps);
+  auto pos_T = [&](int m) {
+    T[m] = vsub(dd[m], dd[m - 1]);
+    T3[m] = vmul(T[m], c13);
+  };
   auto al_qX = [&](int m) {                  // interval (D2_m, R_m), R = 2 D2_m - D2_{m-1}
     const V R = r_end(D2[m], W[m - 1]);
     qX[m] = q_interval_v(D2[m], FD[m], R, f_eval_v(R), eps4);
@@ -319,21 +325,19 @@ __device__ __forceinline__ void sweep_stream(LoadV v_at, V rdx, V eps4, V eps, E
     for (int m = 1; m <= 4; ++m) jp_pair(m);
   }
 
-  const V cm16 = vsplat(-1.0f / 6.0f, eps);
-  const V c13 = vsplat(1.0f / 3.0f, eps), cm13 = vsplat(-1.0f / 3.0f, eps);
-  const V c12 = vsplat(0.5f, eps), cm12 = vsplat(-0.5f, eps);
+  const V cm16 = vsplat(-1.0f / 6.0f, eps), c12 = vsplat(0.5f, eps);
 #pragma unroll
   for (int p = 0; p < K; ++p) {
     // node p: phi^- = (c + T_b/12) - corr^-, phi^+ = (c - T_b/12) + corr^+
     const V mid = vmul(c12, vadd(v[p + 2], v[p + 3]));
-    const V tb = T[p + 3];
+    const V tb2 = vmul(c12, T[p + 3]);
     V nm, rm, np, rp;
     if (WEIGHTS == W_ARCLEN) {
-      side_corr_v(qX[p + 2], qY[p + 2], qZ[p + 3], vmul(T[p + 2], cm13), vmul(cm12, tb), nm, rm);
-      side_corr_v(qZ[p + 4], qY[p + 3], qX[p + 3], vmul(T[p + 4], c13), vmul(c12, tb), np, rp);
+      side_corr_v<true>(qX[p + 2], qY[p + 2], qZ[p + 3], T3[p + 2], tb2, nm, rm);
+      side_corr_v<false>(qZ[p + 4], qY[p + 3], qX[p + 3], T3[p + 4], tb2, np, rp);
     } else {
-      side_corr_v(qX[p + 1], qY[p + 2], qZ[p + 3], vmul(T[p + 2], cm13), vmul(cm12, tb), nm, rm);
-      side_corr_v(qZ[p + 4], qY[p + 3], qX[p + 2], vmul(T[p + 4], c13), vmul(c12, tb), np, rp);
+      side_corr_v<true>(qX[p + 1], qY[p + 2], qZ[p + 3], T3[p + 2], tb2, nm, rm);
+      side_corr_v<false>(qZ[p + 4], qY[p + 3], qX[p + 2], T3[p + 4], tb2, np, rp);
     }
     emit(p, vfma(nm, rm, vfma(dd[p + 2], cm16, mid)), vfma(np, rp, vfma(dd[p + 3], cm16, mid)));
     // advance the window by one position
@@ -367,6 +371,7 @@ __device__ __forceinline__ bool sweep_stream_short(LoadV v_at, V rdx, V eps4, Em
   V s[K + 5];
   V dd[K + 5];
   V T[K + 5];
+  V T3[K + 5];
   V D2[K + 6];
   V W[K + 6];
   V S[K + 6];                                // S_m = sqrt(1 + D2_m^2)
@@ -388,17 +393,21 @@ __device__ __forceinline__ bool sweep_stream_short(LoadV v_at, V rdx, V eps4, Em
       ok &= short_width(W[m - 1]);
     }
   };
-  auto pos_T = [&](int m) { T[m] = vsub(dd[m], dd[m - 1]); };
+  const V c13 = vsplat(1.0f / 3.0f, rdx);
+  auto pos_T = [&](int m) {
+    T[m] = vsub(dd[m], dd[m - 1]);
+    T3[m] = vmul(T[m], c13);
+  };
   auto al_qX = [&](int m) { qX[m] = qv(S[m], sq(r_end(D2[m], W[m - 1]))); };
   auto al_qY = [&](int m) { qY[m] = qv(S[m], S[m + 1]); };
   auto al_qZ = [&](int m) { qZ[m] = qv(sq(l_end(D2[m], W[m])), S[m]); };
-  // side_corr_v when the denominator is known to be in range
-  auto corr = [&](V q0, V q1, V q2, V ta3, V tb2, V &num, V &rd) {
+  // side_corr_v when the denominator is known to be in range (neg: r = -1 / den)
+  auto corr = [&](V q0, V q1, V q2, V ta3, V tb2, bool neg, V &num, V &rd) {
     const V A0 = vmul(q1, q2), A1 = vmul(q0, q2), A2 = vmul(q0, q1);
     const V den = vfma(vsplat(6.0f, q0), A1, vfma(vsplat(3.0f, q0), A2, A0));
     num = vfma(A0, ta3, vmul(A2, tb2));
 #pragma unroll
-    for (int i = 0; i < LN::n; ++i) LN::at(rd, i) = sfu_rcp(LN::get(den, i));
+    for (int i = 0; i < LN::n; ++i) LN::at(rd, i) = sfu_rcp(neg ? -LN::get(den, i) : LN::get(den, i));
   };
 
 #pragma unroll
@@ -414,16 +423,14 @@ __device__ __forceinline__ bool sweep_stream_short(LoadV v_at, V rdx, V eps4, Em
   ok &= short_sizes(D2[2], eps4);
   if (!__all_sync(0xffffffffu, ok)) return false;
 
-  const V cm16 = vsplat(-1.0f / 6.0f, rdx);
-  const V c13 = vsplat(1.0f / 3.0f, rdx), cm13 = vsplat(-1.0f / 3.0f, rdx);
-  const V c12 = vsplat(0.5f, rdx), cm12 = vsplat(-0.5f, rdx);
+  const V cm16 = vsplat(-1.0f / 6.0f, rdx), c12 = vsplat(0.5f, rdx);
 #pragma unroll
   for (int p = 0; p < K; ++p) {
     const V mid = vmul(c12, vadd(v[p + 2], v[p + 3]));
-    const V tb = T[p + 3];
+    const V tb2 = vmul(c12, T[p + 3]);
     V nm, rm, np, rp;
-    corr(qX[p + 2], qY[p + 2], qZ[p + 3], vmul(T[p + 2], cm13), vmul(cm12, tb), nm, rm);
-    corr(qZ[p + 4], qY[p + 3], qX[p + 3], vmul(T[p + 4], c13), vmul(c12, tb), np, rp);
+    corr(qX[p + 2], qY[p + 2], qZ[p + 3], T3[p + 2], tb2, true, nm, rm);
+    corr(qZ[p + 4], qY[p + 3], qX[p + 3], T3[p + 4], tb2, false, np, rp);
     emit(p, vfma(nm, rm, vfma(dd[p + 2], cm16, mid)), vfma(np, rp, vfma(dd[p + 3], cm16, mid)));
     if (p + 1 < K) {
       v[p + 6] = v_at(p + 6);
