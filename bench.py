@@ -314,19 +314,22 @@ def bench_batched(args, stream):
         tuning = b.tuning()
         mem = b.memory_bytes()
     t_batch = time.perf_counter() - t0
-    # each tile width the autotuner chooses from, fixed, on the same batch: the time loop alone
-    # (alw_batch_run after the arena is built), twice per width in alternating order
-    widths = {"64x32": [], "32x32": []}
-    for w in (64, 32, 64, 32):
+    # the tile widths and launch forms the autotuner chooses from, each fixed, on the same batch: the
+    # time loop alone (alw_batch_run after the arena is built), twice each in alternating order
+    forms = [(64, False), (32, False), (64, True)]
+    widths = {f"{w}x32{', one launch per stage' if one else ', one launch per Hamiltonian'}": []
+              for w, one in forms}
+    for w, one in forms + forms:
         with native.Batch(precision="mixed", weights=args.weights, stream=stream) as bw:
             for inst, ph in zip(insts, phis):
                 bw.add(nx=inst.n, ny=inst.n, ham=inst.ham, phi0=ph, t_final=inst.t_final, **kw)
             bw.set_tuning(order=tuning["order"], steps_per_graph=tuning["steps_per_graph"], run=tuning["run"],
-                          tile_w=w)
+                          tile_w=w, one_launch=one)
             bw.build()
             t1 = time.perf_counter()
             bw.run()
-            widths[f"{w}x32"].append(time.perf_counter() - t1)
+            widths[f"{w}x32{', one launch per stage' if one else ', one launch per Hamiltonian'}"].append(
+                time.perf_counter() - t1)
     widths = {k: {"run_s": v, "solves_per_s": len(insts) / min(v)} for k, v in widths.items()}
     serial_n = min(len(insts), args.serial_count)
     t0 = time.perf_counter()
@@ -341,7 +344,7 @@ def bench_batched(args, stream):
     return {"instances": len(insts), "solves_per_s": len(insts) / t_batch,
             "serial_solves_per_s": serial_n / t_serial, "speedup_vs_serial": (len(insts) / t_batch) / (serial_n / t_serial),
             "point_updates_per_s": node_steps / t_batch, "wall_s": t_batch, "graph_replays": replays,
-            "tuning": tuning, "tile_widths_fixed": widths, "device_bytes": mem, "serial_sample": serial_n,
+            "tuning": tuning, "fixed_tunings_time_loop": widths, "device_bytes": mem, "serial_sample": serial_n,
             "finite": ok}
 
 

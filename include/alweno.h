@@ -251,6 +251,10 @@ typedef struct {
   int32_t tile_w;           /* tile width in nodes: 64 (tiles 64 x 32) or 32 (tiles 32 x 32: twice the
                                tiles, each with 1.1x the halo reads per node); 0 = 64.  The
                                autotuner times both on the batch's own work list. */
+  int32_t one_launch;       /* 1: one launch per RK stage over every instance, the kernel choosing
+                               each tile's Hamiltonian at run time; 0: one launch per Hamiltonian
+                               present, each with a kernel specialised for it.  The autotuner
+                               times both when the batch mixes Hamiltonians. */
 } alw_batch_tuning;
 
 alw_status alw_batch_create(const alw_scheme *scheme, void *cuda_stream, alw_batch **out);
@@ -260,7 +264,7 @@ alw_status alw_batch_create(const alw_scheme *scheme, void *cuda_stream, alw_bat
 alw_status alw_batch_add(alw_batch *b, const alw_grid *grid, const alw_hamiltonian *ham, const double *host_phi0,
                          size_t n, double t_final, int32_t *id_out);
 /* Fix the tuning (NULL: let the autotuner choose on the next run).  ALW_EINVAL
- * for a field outside its range (tile_w other than 0, 32, 64). */
+ * for a field outside its range (tile_w other than 0, 32, 64; one_launch other than 0, 1). */
 alw_status alw_batch_set_tuning(alw_batch *b, const alw_batch_tuning *tuning);
 alw_status alw_batch_get_tuning(alw_batch *b, alw_batch_tuning *tuning);
 /* Lay out the device arena, upload every instance and tune the work list now

@@ -14,7 +14,10 @@
 // store, so the state of the batch is untouched -- and chooses the number of
 // RK steps per graph replay from the amount of work per step.  Results are
 // cached per batch shape.  The arena is laid out for 64-wide tiles, which
-// covers the narrow ones, so both widths run on the same arrays.
+// covers the narrow ones, so both widths run on the same arrays.  A batch of
+// several Hamiltonians runs either one launch per stage (the kernel choosing
+// each tile's Hamiltonian) or one launch per Hamiltonian (a kernel specialised
+// for it); the autotuner times both.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -243,12 +246,18 @@ std::vector<int> work_list(const alw_batch *b, const std::vector<char> &live, in
 }
 
 // Uploads the work list of the live instances as one group per Hamiltonian (each in the given
-// order and run layout), so that every launch runs the kernel specialised for its Hamiltonian.
-// Returns the number of entries.
+// order and run layout), so that every launch runs the kernel specialised for its Hamiltonian --
+// or, with tuning.one_launch, as one group (kind -1) that a single launch per stage runs with the
+// Hamiltonian chosen per tile.  Returns the number of entries.
 alw_status upload_groups(alw_batch *b, const std::vector<char> &live, int order, int run, int *total) {
   std::vector<int> all;
   b->groups.clear();
-  for (int kind = 0; kind < 16; ++kind) {
+  if (b->tuning.one_launch) {
+    const std::vector<int> list = work_list(b, live, order, run);
+    b->groups.push_back({0, (int)list.size(), -1});
+    all = list;
+  }
+  for (int kind = 0; kind < 16 && !b->tuning.one_launch; ++kind) {
     std::vector<char> sel(live.size(), 0);
     bool any = false;
     for (size_t i = 0; i < live.size(); ++i)
@@ -504,33 +513,40 @@ alw_status autotune(alw_batch *b) {
   double best_ms = 1e30;
   const int widths[2] = {kTile2DX, kTile2DXNarrow};
   const int orders[3] = {ALW_ORDER_INSTANCE, ALW_ORDER_LARGEST_FIRST, ALW_ORDER_INTERLEAVED};
+  // one launch per stage is a choice only when the batch mixes Hamiltonians
+  bool mixed_hams = false;
+  for (auto &d : b->h_inst) mixed_hams |= d.ham != b->h_inst[0].ham;
+  const int launches_n = mixed_hams ? 2 : 1;
   // runs of 4 entries per CTA: each CTA changes instance (and closes a run) a quarter as often
   // as with single entries while neighbouring blocks of tiles still run side by side (one
   // contiguous stretch per CTA times fast in these reduction-only trials but loses in full
   // stages, so the run length is fixed rather than tuned)
   const int runs[1] = {kDefaultRun};
   b->tuning.grid_ctas = 0;
-  for (int w : widths) {
-    b->tuning.tile_w = w;
-    b->grid_cap = cap_for(b);
-    if (b->grid_cap <= 0) continue;
-    for (int o : orders)
-      for (int l : runs) {
-        alw_status st = upload_groups(b, live, o, l, nullptr);
-        if (st) return st;
-        double ms;
-        st = trial(b, 1, &ms);  // warm-up
-        if (st) return st;
-        st = trial(b, 3, &ms);
-        if (st) return st;
-        if (ms < best_ms) {
-          best_ms = ms;
-          best.order = o;
-          best.run = l;
-          best.tile_w = w;
+  for (int one = 0; one < launches_n; ++one)
+    for (int w : widths) {
+      b->tuning.tile_w = w;
+      b->tuning.one_launch = one;
+      b->grid_cap = cap_for(b);
+      if (b->grid_cap <= 0) continue;
+      for (int o : orders)
+        for (int l : runs) {
+          alw_status st = upload_groups(b, live, o, l, nullptr);
+          if (st) return st;
+          double ms;
+          st = trial(b, 1, &ms);  // warm-up
+          if (st) return st;
+          st = trial(b, 3, &ms);
+          if (st) return st;
+          if (ms < best_ms) {
+            best_ms = ms;
+            best.order = o;
+            best.run = l;
+            best.tile_w = w;
+            best.one_launch = one;
+          }
         }
-      }
-  }
+    }
   best.steps_per_graph = total >= 4096 ? 2 : (total >= 512 ? 8 : 32);
   best.grid_ctas = 0;  // occupancy cap
   b->tuning = best;
@@ -620,7 +636,8 @@ alw_status alw_batch_set_tuning(alw_batch *b, const alw_batch_tuning *t) {
   }
   if (t->order < ALW_ORDER_INSTANCE || t->order > ALW_ORDER_INTERLEAVED || t->steps_per_graph < 1 ||
       t->steps_per_graph > 256 || t->grid_ctas < 0 ||
-      t->run < 0 || t->run > 64 || (t->tile_w != 0 && t->tile_w != kTile2DX && t->tile_w != kTile2DXNarrow))
+      t->run < 0 || t->run > 64 || (t->tile_w != 0 && t->tile_w != kTile2DX && t->tile_w != kTile2DXNarrow) ||
+      (t->one_launch != 0 && t->one_launch != 1))
     return berr(ALW_EINVAL, "bad tuning");
   b->tuning = *t;
   if (b->tuning.tile_w == 0) b->tuning.tile_w = kTile2DX;

@@ -39,8 +39,10 @@ static int launch2d_one(const Stage2DParams &prm, cudaStream_t stream) {
 
 template <int PREC, int W, int TX>
 static int launch2d_h(const Stage2DParams &prm, cudaStream_t s) {
-  // a single instance's Hamiltonian, or the one every entry of a batch group shares (the narrow
-  // tiles serve batches, which take the position-free Hamiltonians only)
+  // a single instance's Hamiltonian, or the one every entry of a batch group shares, or (batch_kind1
+  // 0) each entry's own, dispatched in the kernel (the narrow tiles and the runtime dispatch serve
+  // batches, which take the position-free Hamiltonians only)
+  if (prm.insts && prm.batch_kind1 == 0) return launch2d_one<PREC, W, H_RUNTIME, TX>(prm, s);
   switch (prm.insts ? prm.batch_kind1 - 1 : prm.inst0.ham) {
     case H_BURGERS2D: return launch2d_one<PREC, W, H_BURGERS2D, TX>(prm, s);
     case H_NEGCOS2D: return launch2d_one<PREC, W, H_NEGCOS2D, TX>(prm, s);

@@ -31,7 +31,8 @@ struct Stage2DParams {
   int ntiles;               // work-list length
   int grid_ctas;            // persistent CTAs to launch (0: as many as fit; never more than fit or ntiles)
   int tile_w;               // tile width: 64 (0 means 64) or 32; the maps' boxes and insts[].tiles_x match it
-  int batch_kind1;          // batch: 1 + the Hamiltonian every listed instance has
+  int batch_kind1;          // batch: 1 + the Hamiltonian every listed instance has; 0: instances of any
+                            // position-free 2D Hamiltonian, dispatched per tile in the kernel
   const InstDesc *insts;    // batch: instance table (nullptr: the single instance `inst0`)
   DevState *states;         // batch: state of instance i at states + i (nullptr: read insts[i].st)
   const int *tiles;         // batch: work list, entry = instance * 65536 + tile of that instance

@@ -120,15 +120,42 @@ template <> struct Ham2<H_OPTCTRL2D> {
   }
 };
 
-// The Hamiltonian of a launch (compile-time kind; batches launch one group per Hamiltonian).
+// The Hamiltonian of a launch: a compile-time kind, or H_RUNTIME, for batches that run instances
+// of several Hamiltonians in one launch: the kind of the tile's instance, dispatched per node (the
+// branch is uniform across a tile, so warps never diverge on it).
+constexpr int H_RUNTIME = -1;
 template <int H> struct HamSel {
   static constexpr bool kSameAlpha = Ham2<H>::kSameAlpha;
+  __device__ __forceinline__ explicit HamSel(int) {}
   __device__ __forceinline__ float value_sums(float su, float sv, float x, float y) const {
     return Ham2<H>::value_sums(su, sv, x, y);
   }
   __device__ __forceinline__ void alpha(float um, float up, float vm, float vp, float x, float y, float &ax,
                                         float &ay) const {
     Ham2<H>::alpha(um, up, vm, vp, x, y, ax, ay);
+  }
+};
+// runtime kind: the position-free 2D Hamiltonians batches take
+template <> struct HamSel<H_RUNTIME> {
+  static constexpr bool kSameAlpha = false;
+  int kind;
+  __device__ __forceinline__ explicit HamSel(int k) : kind(k) {}
+  __device__ __forceinline__ float value_sums(float su, float sv, float x, float y) const {
+    switch (kind) {
+      case H_BURGERS2D: return Ham2<H_BURGERS2D>::value_sums(su, sv, x, y);
+      case H_NEGCOS2D: return Ham2<H_NEGCOS2D>::value_sums(su, sv, x, y);
+      case H_SIN2D: return Ham2<H_SIN2D>::value_sums(su, sv, x, y);
+      default: return Ham2<H_EIKONAL2D>::value_sums(su, sv, x, y);
+    }
+  }
+  __device__ __forceinline__ void alpha(float um, float up, float vm, float vp, float x, float y, float &ax,
+                                        float &ay) const {
+    switch (kind) {
+      case H_BURGERS2D: Ham2<H_BURGERS2D>::alpha(um, up, vm, vp, x, y, ax, ay); break;
+      case H_NEGCOS2D: Ham2<H_NEGCOS2D>::alpha(um, up, vm, vp, x, y, ax, ay); break;
+      case H_SIN2D: Ham2<H_SIN2D>::alpha(um, up, vm, vp, x, y, ax, ay); break;
+      default: Ham2<H_EIKONAL2D>::alpha(um, up, vm, vp, x, y, ax, ay); break;
+    }
   }
 };
 
@@ -369,7 +396,7 @@ __global__ void __launch_bounds__(Geo2D<TXv>::NT, Geo2D<TXv>::MINB)
     const TileInfo &d = s_info[buf];  // this tile's instance fields (shared memory)
     const int nx = d.nx, ny = d.ny, tx0 = d.tx0, ty0 = d.ty0;
     const size_t rbase = (size_t)d.row_off * p.pitch;   // element offset of the instance's rows
-    const HamSel<H> ham;
+    const HamSel<H> ham(d.ham);
     const float dtf = s_info[buf].dtf, fax = s_info[buf].fax, fay = s_info[buf].fay;
     const float *A = raw + buf * NARR * ARR;
     const float *B = A + ARR;
@@ -476,7 +503,8 @@ __global__ void __launch_bounds__(Geo2D<TXv>::NT, Geo2D<TXv>::MINB)
 
     // ---- 3. nodes (colY, K*segY + q): Lax-Friedrichs Hamiltonian, RK combination, store; one
     // unrolled loop per stage and per edge/interior tile, so that no node tests either
-    auto finish = [&](auto stage_c, auto edge_c) {
+    auto finish = [&](auto stage_c, auto edge_c, auto hsel) {
+      using HS = decltype(hsel);
       constexpr int ST = decltype(stage_c)::value;
       constexpr bool EDGE = decltype(edge_c)::value;
 #pragma unroll
@@ -488,15 +516,16 @@ __global__ void __launch_bounds__(Geo2D<TXv>::NT, Geo2D<TXv>::MINB)
         const float2 u = su[y * SUP + colY];
         const float xn = fmaf((float)gi, d.dx, d.xlo), yn = fmaf((float)gj, d.dy, d.ylo);
         float ax, ay;
-        ham.alpha(u.x, u.y, dmq, dpq, xn, yn, ax, ay);
+        hsel.alpha(u.x, u.y, dmq, dpq, xn, yn, ax, ay);
         const float aX = local_alpha ? ax : fax, aY = local_alpha ? ay : fay;
-        const float Hv = ham.value_sums(u.y + u.x, dpq + dmq, xn, yn);
+        const float Hv = hsel.value_sums(u.y + u.x, dpq + dmq, xn, yn);
         const float L = fmaf(aX * 0.5f, u.y - u.x, fmaf(aY * 0.5f, dpq - dmq, -Hv));
         if (inside) {
           // L depends on all four one-sided derivatives: L * 0 is NaN exactly when L is not finite
           nfin = fmaf(L, 0.0f, nfin);
           amx = fmaxf(amx, ax);
-          if (!HamSel<H>::kSameAlpha) amy = fmaxf(amy, ay);
+          // (with a runtime Hamiltonian the fold below does not copy amx, so amy is always kept)
+          if (!HS::kSameAlpha || !HamSel<H>::kSameAlpha) amy = fmaxf(amy, ay);
         }
         if (ST == 0 || !inside) continue;
         const int sidx = (y + 3) * SW + colY + 4;
@@ -537,9 +566,22 @@ __global__ void __launch_bounds__(Geo2D<TXv>::NT, Geo2D<TXv>::MINB)
         }
       }
     };
+    // the Hamiltonian of the tile: the launch's, or with H_RUNTIME the instance's, chosen once per tile
+    auto finish_h = [&](auto stage_c, auto edge_c) {
+      if constexpr (H == H_RUNTIME) {
+        switch (d.ham) {
+          case H_BURGERS2D: finish(stage_c, edge_c, HamSel<H_BURGERS2D>(0)); break;
+          case H_NEGCOS2D: finish(stage_c, edge_c, HamSel<H_NEGCOS2D>(0)); break;
+          case H_SIN2D: finish(stage_c, edge_c, HamSel<H_SIN2D>(0)); break;
+          default: finish(stage_c, edge_c, HamSel<H_EIKONAL2D>(0)); break;
+        }
+      } else {
+        finish(stage_c, edge_c, ham);
+      }
+    };
     auto finish_stage = [&](auto stage_c) {
-      if (edge) finish(stage_c, std::true_type{});
-      else finish(stage_c, std::false_type{});
+      if (edge) finish_h(stage_c, std::true_type{});
+      else finish_h(stage_c, std::false_type{});
     };
     switch (p.stage) {
       case 0: finish_stage(std::integral_constant<int, 0>{}); break;

@@ -65,7 +65,7 @@ class State(ctypes.Structure):
 
 class BatchTuning(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int32), ("steps_per_graph", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
-                ("run", ctypes.c_int32), ("tile_w", ctypes.c_int32)]
+                ("run", ctypes.c_int32), ("tile_w", ctypes.c_int32), ("one_launch", ctypes.c_int32)]
 
 
 ORDER = {"instance": 0, "largest_first": 1, "interleaved": 2}
@@ -369,11 +369,11 @@ class Batch:
         return i.value
 
     def set_tuning(self, order: str = None, steps_per_graph: int = 4, grid_ctas: int = 0, run: int = 4,
-                   tile_w: int = 64):
+                   tile_w: int = 64, one_launch: bool = False):
         if order is None:
             check(self._L.alw_batch_set_tuning(self._h, None))
             return
-        t = BatchTuning(ORDER[order], steps_per_graph, grid_ctas, run, tile_w)
+        t = BatchTuning(ORDER[order], steps_per_graph, grid_ctas, run, tile_w, int(bool(one_launch)))
         check(self._L.alw_batch_set_tuning(self._h, ctypes.byref(t)))
 
     def tuning(self) -> dict:
@@ -381,7 +381,8 @@ class Batch:
         check(self._L.alw_batch_get_tuning(self._h, ctypes.byref(t)))
         inv = {v: k for k, v in ORDER.items()}
         return {"order": inv.get(t.order, t.order), "steps_per_graph": t.steps_per_graph, "grid_ctas": t.grid_ctas,
-                "run": t.run, "tile": f"{t.tile_w or 64}x32"}
+                "run": t.run, "tile": f"{t.tile_w or 64}x32",
+                "launches_per_stage": "one" if t.one_launch else "one per Hamiltonian"}
 
     def build(self):
         """Upload the instances and tune the work list now (run() does it on first use)."""

@@ -166,3 +166,26 @@ def test_batch_instances_match_oracle(weights):
         assert st.t == inst.t_final
         err = float(np.max(np.abs(got - ref)))
         assert err <= MIXED_SOLVE_TOL, (k, inst, err)
+
+
+@pytest.mark.parametrize("tile_w", [64, 32])
+def test_batch_one_launch_per_stage_matches_per_hamiltonian_launches(tile_w):
+    # both Hamiltonians of the batched workload in one launch per RK stage (the kernel choosing each
+    # tile's Hamiltonian) against one launch per Hamiltonian: another kernel instantiation over the
+    # same segments, so the results agree to rounding (the mixed-solve bound against the oracle)
+    insts = _mix(10, 24, 200, seed=47)
+    assert {i.ham for i in insts} == {"burgers2d", "negcos2d"}
+    outs = {}
+    for one in (False, True):
+        with native.Batch(precision="mixed") as b:
+            for inst in insts:
+                phi0, _ = inputs.instance_phi0(inst)
+                b.add(nx=inst.n, ny=inst.n, xlo=-2.0, xhi=2.0, ylo=-2.0, yhi=2.0, ham=inst.ham, phi0=phi0,
+                      t_final=inst.t_final)
+            b.set_tuning(order="interleaved", steps_per_graph=3, run=4, tile_w=tile_w, one_launch=one)
+            b.run()
+            assert b.tuning()["launches_per_stage"] == ("one" if one else "one per Hamiltonian")
+            outs[one] = [(b.get_phi(k), b.get_state(k)) for k in range(len(insts))]
+    for inst, (a, sa), (c, sc) in zip(insts, outs[False], outs[True]):
+        assert sa.t == sc.t == inst.t_final
+        assert np.max(np.abs(a - c)) <= MIXED_SOLVE_TOL
