@@ -403,9 +403,10 @@ __global__ void __launch_bounds__(Geo2D<TXv>::NT, Geo2D<TXv>::MINB)
     const float *C = A + 2 * ARR;
     const bool has_delta = PREC == P_MIXED && prm.map_c >= 0;
 
-    // ---- 1. x differences (rows by warp, columns by lane: no division, conflict-free); the
-    // MIXED variant without a delta array (stage 1) is a separate loop, so that it reads two
-    // arrays, not three
+    // ---- 1. x differences in the units of the sweep (arc length: Delta^+ phi / dx^2; Jiang-Peng:
+    // Delta^+ phi / dx), rows by warp, columns by lane (no division, conflict-free); the MIXED variant
+    // without a delta array (stage 1) is a separate loop, so that it reads two arrays, not three
+    const float rdx2 = (W == W_ARCLEN) ? d.rdx * d.rdx : d.rdx;
     auto diff_pass = [&](auto with_delta) {
       constexpr bool WD = decltype(with_delta)::value;
       auto cell_diff = [&](int i0, int i1) -> float {
@@ -423,13 +424,13 @@ __global__ void __launch_bounds__(Geo2D<TXv>::NT, Geo2D<TXv>::MINB)
 #pragma unroll
         for (int c = lane; c < TX; c += 32) {
           const int i0 = (r + 3) * SW + c + 1;
-          dX[r * DXP + c] = cell_diff(i0, i0 + 1) * d.rdx;
+          dX[r * DXP + c] = cell_diff(i0, i0 + 1) * rdx2;
         }
       }
       for (int j = tid; j < TY * (DXW - TX); j += NT) {
         const int r = j / (DXW - TX), c = TX + j % (DXW - TX);
         const int i0 = (r + 3) * SW + c + 1;
-        dX[r * DXP + c] = cell_diff(i0, i0 + 1) * d.rdx;
+        dX[r * DXP + c] = cell_diff(i0, i0 + 1) * rdx2;
       }
     };
     if (has_delta) diff_pass(std::true_type{});
@@ -455,10 +456,10 @@ __global__ void __launch_bounds__(Geo2D<TXv>::NT, Geo2D<TXv>::MINB)
     {
       const float *vx = dX + lane * DXP + K * warp;
       // the y differences of the column segment, formed here from the tile arrays like the x
-      // differences of the differences pass; v_at is called for m = 0, 1, 2, ... in order, so each
-      // position loads one new row and reuses the previous one
+      // differences of the differences pass (in the same units); u_at is called for m = 0, 1, 2, ... in
+      // order, so each position loads one new row and reuses the previous one
       const int iy = (K * segY) * SW + colY + 4;
-      const float rdy = d.rdy;
+      const float rdy2 = (W == W_ARCLEN) ? d.rdy * d.rdy : d.rdy;
       auto make_vat = [&]() {
         float pa = A[iy], pb = 0.0f, pc = 0.0f;
         if (PREC == P_MIXED) {
@@ -479,7 +480,7 @@ __global__ void __launch_bounds__(Geo2D<TXv>::NT, Geo2D<TXv>::MINB)
             dy = a1 - pa;
             pa = a1;
           }
-          return make_float2(vx[m], dy * rdy);
+          return make_float2(vx[m], dy * rdy2);
         };
       };
       auto emit = [&](int q, float2 dm, float2 dp) {
@@ -487,8 +488,11 @@ __global__ void __launch_bounds__(Geo2D<TXv>::NT, Geo2D<TXv>::MINB)
         ym[q] = dm.y;
         yp[q] = dp.y;
       };
-      const float2 rd = make_float2(d.rdx, d.rdy);
-      const float2 e4 = make_float2(4.0f * eps * d.rdx * d.rdx, 4.0f * eps * d.rdy * d.rdy);
+      SweepConsts<float2> sc;
+      sc.eps4 = make_float2(4.0f * eps * d.rdx * d.rdx, 4.0f * eps * d.rdy * d.rdy);
+      sc.h2 = make_float2(0.5f * d.dx, 0.5f * d.dy);
+      sc.h3 = make_float2(d.dx * (1.0f / 3.0f), d.dy * (1.0f / 3.0f));
+      sc.mh6 = make_float2(d.dx * (-1.0f / 6.0f), d.dy * (-1.0f / 6.0f));
       // arc length, MIXED: every warp sweeps with the short-interval form first and sweeps again in
       // full when some segment of the warp does not qualify (that form then replaces all its
       // results).  Which form produced a node's values thus depends only on the data of the warp's
@@ -496,8 +500,11 @@ __global__ void __launch_bounds__(Geo2D<TXv>::NT, Geo2D<TXv>::MINB)
       // which tiles or instances are processed, nor on history: a single solve, a batch, a server
       // round and a resumed checkpoint (all with 64-wide tiles) choose alike.
       bool full = true;
-      if (SHORT) full = !sweep_stream_short<K, float2>(make_vat(), rd, e4, emit);
-      if (full) sweep_stream<K, W, float2>(make_vat(), rd, e4, make_float2(eps, eps), emit);
+      if (SHORT) full = !sweep_stream_short<K, float2>(make_vat(), sc, emit);
+      if (full) {
+        if constexpr (W == W_ARCLEN) sweep_stream<K, float2>(make_vat(), sc, emit);
+        else sweep_stream_jp<K, float2>(make_vat(), make_float2(eps, eps), emit);
+      }
     }
     __syncthreads();
 

@@ -41,6 +41,8 @@
 // their results agree to rounding (the compiler may select instructions for the two code paths
 // differently), and the stage kernel decides between them from the segment's own data only.
 #pragma once
+#include <type_traits>
+
 #include "alw_device.cuh"
 
 namespace alw {
@@ -193,45 +195,60 @@ static __device__ __noinline__ float side_corr_wide(float q0, float q1, float q2
   return (a0 * r) * ta3 + (a2 * r) * (1.0f / 3.0f) * tb2;
 }
 
-// The side's correction (A0 T_a / 3 + A2 T_b / 2) / den as a pair (num, r) with correction =
-// num * r (r = 1 / den; on the rare lanes whose products leave the float range, num = the
-// correction and r = 1); ta3 = T_a / 3, tb2 = T_b / 2.  NEG (the "-" side, whose correction is
-// subtracted) gives r = -1 / den (or -1), so that the caller adds num * r to the central part with
-// one fused multiply-add on either side.
-template <bool NEG, class V>
-__device__ __forceinline__ void side_corr_v(V q0, V q1, V q2, V ta3, V tb2, V &num_out, V &r_out) {
+// Per-lane constants of an arc-length sweep (x lane: dx; y lane: dy).
+template <class V> struct SweepConsts {
+  V eps4;          // 4 eps / dx^2
+  V h2, h3, mh6;   // dx / 2, dx / 3, -dx / 6 (the central parts and T_a / 3, T_b / 2 back in units of phi_x)
+};
+
+// The corrections of the two sides that read one stencil of indicators.  The "-" side of node j reads
+// (q0, q1, q2) = (g0, g1, g2) and the "+" side of node j - 1 reads the same three indicators mirrored,
+// (q0, q1, q2) = (g2, g1, g0); the products g1 g2, g0 g2, g0 g1 therefore serve both sides:
+//   "-": A0 = g1 g2, A1 = g0 g2, A2 = g0 g1;     "+": A0 = g0 g1, A1 = g0 g2, A2 = g1 g2,
+// den = A0 + 6 A1 + 3 A2 and num = A0 T_a / 3 + A2 T_b / 2 on either side (ta = T_a / 3, tb = T_b / 2 of
+// that side).  Each side's correction num / den is returned as a pair (num, r) with correction = num * r:
+// r = -1 / den on the "-" side (whose correction is subtracted) and 1 / den on the "+" side, so that the
+// caller adds num * r to the central part with one fused multiply-add.  CHECKED: on lanes whose
+// denominator leaves the safe float range (or is NaN), num = the correction from side_corr_wide and
+// r = -1 or 1.  MINUS / PLUS select the sides wanted.  (The sweeps with the range check form each
+// side on its own -- sharing the products there measured slower, the rare out-of-line fallback
+// making the shared values live across its call -- and the short-interval sweep forms both.)
+template <bool CHECKED, bool MINUS, bool PLUS, class V>
+__device__ __forceinline__ void group_corr_v(V g0, V g1, V g2, V ta_m, V tb_m, V ta_p, V tb_p, V &num_m, V &r_m,
+                                             V &num_p, V &r_p) {
   using LN = Lanes<V>;
-  const V A0 = vmul(q1, q2), A1 = vmul(q0, q2), A2 = vmul(q0, q1);
-  const V den = vfma(vsplat(6.0f, q0), A1, vfma(vsplat(3.0f, q0), A2, A0));
-  const V num = vfma(A0, ta3, vmul(A2, tb2));
-  // den >= A0 > 0 cannot underflow (arc length: q >= 16; Jiang-Peng: q >= eps^2), so only the
-  // upper end of the float range needs a check (NaN fails it too)
-  V rd;
-  bool ok = true;
-#pragma unroll
-  for (int i = 0; i < LN::n; ++i) {
-    const float dn = LN::get(den, i);
-    ok = ok && (dn < 1e30f);
-    LN::at(rd, i) = sfu_rcp(NEG ? -dn : dn);
-  }
-  V nm = num;
-  if (!ok) {
+  const V p12 = vmul(g1, g2), p02 = vmul(g0, g2), p01 = vmul(g0, g1);
+  // den >= A0 > 0 cannot underflow (arc length: q >= 16; Jiang-Peng: q >= eps^2), so only the upper end
+  // of the float range needs a check (NaN fails it too)
+  auto side = [&](V a0, V a2, V ta, V tb, bool neg, V q0, V q1, V q2, V &num_out, V &r_out) {
+    const V den = vfma(vsplat(6.0f, q0), p02, vfma(vsplat(3.0f, q0), a2, a0));
+    V nm = vfma(a0, ta, vmul(a2, tb));
+    V rd;
+    bool ok = true;
 #pragma unroll
     for (int i = 0; i < LN::n; ++i) {
       const float dn = LN::get(den, i);
-      if (!(dn < 1e30f)) {
-        LN::at(nm, i) = side_corr_wide(LN::get(q0, i), LN::get(q1, i), LN::get(q2, i), LN::get(ta3, i),
-                                       LN::get(tb2, i));
-        LN::at(rd, i) = NEG ? -1.0f : 1.0f;
+      if (CHECKED) ok = ok && (dn < 1e30f);
+      LN::at(rd, i) = sfu_rcp(neg ? -dn : dn);
+    }
+    if (CHECKED && !ok) {
+#pragma unroll
+      for (int i = 0; i < LN::n; ++i) {
+        const float dn = LN::get(den, i);
+        if (!(dn < 1e30f)) {
+          LN::at(nm, i) = side_corr_wide(LN::get(q0, i), LN::get(q1, i), LN::get(q2, i), LN::get(ta, i),
+                                         LN::get(tb, i));
+          LN::at(rd, i) = neg ? -1.0f : 1.0f;
+        }
       }
     }
-  }
-  num_out = nm;
-  r_out = rd;
+    num_out = nm;
+    r_out = rd;
+  };
+  if (MINUS) side(p12, p01, ta_m, tb_m, true, g0, g1, g2, num_m, r_m);
+  if (PLUS) side(p01, p12, ta_p, tb_p, false, g2, g1, g0, num_p, r_p);
 }
 
-// v_at(m) returns Delta^+ phi at position i0 - 3 + m (m = 0..K+4) per lane; emit(p, dm, dp)
-// receives node i0 + p.  rdx = 1/dx, eps4 = 4 eps / dx^2 (per lane).
 // Every lane of v holds a width at most kShortH (NaN fails).
 template <class V>
 __device__ __forceinline__ bool short_width(V h) {
@@ -254,105 +271,145 @@ __device__ __forceinline__ bool short_sizes(V d2, V eps4) {
 }
 
 // The extrapolated interval ends R_m = 2 D2_m - D2_{m-1} and L_m = 2 D2_m - D2_{m+1}, formed as
-// D2_m plus or minus the neighbouring width W = d / dx (the quantity the short-interval test
-// inspects; one operation each).
+// D2_m plus or minus the neighbouring width W (the quantity the short-interval test inspects; one
+// operation each).
 template <class V>
 __device__ __forceinline__ V r_end(V d2m, V w_prev) { return vadd(d2m, w_prev); }
 template <class V>
 __device__ __forceinline__ V l_end(V d2m, V w_m) { return vsub(d2m, w_m); }
 
-template <int K, int WEIGHTS, class V, class LoadV, class Emit>
-__device__ __forceinline__ void sweep_stream(LoadV v_at, V rdx, V eps4, V eps, Emit emit) {
+// The window of the arc-length sweeps.  u_at(m) returns u = Delta^+ phi / dx^2 at position i0 - 3 + m
+// (m = 0..K+4) per lane; in these units the second differences D2_m = u_m - u_{m-1} and the widths
+// W_m = D2_{m+1} - D2_m need no scaling, and T_m = W_m - W_{m-1} is T / dx of the first-difference
+// form.  Per position: D2_m, W_{m-1} and the two scaled copies of T_{m-1}, ta = T dx / 3, tb = T dx / 2.
+template <int N, class V>
+struct Window {
+  V u[N], D2[N], W[N], Ta[N], Tb[N];
+  __device__ __forceinline__ void pos(int m, const SweepConsts<V> &c) {
+    D2[m] = vsub(u[m], u[m - 1]);
+    if (m >= 2) W[m - 1] = vsub(D2[m], D2[m - 1]);
+    if (m >= 3) {
+      const V T = vsub(W[m - 1], W[m - 2]);
+      Ta[m - 1] = vmul(T, c.h3);
+      Tb[m - 1] = vmul(T, c.h2);
+    }
+  }
+  // node p: phi^- = (c + T_b / 12) - corr^-, phi^+ = (c - T_b / 12) + corr^+, with
+  // c +- T_b / 12 = dx ((u_{p+2} + u_{p+3}) / 2 - W_{p+2 or p+3} / 6)
+  template <class Emit>
+  __device__ __forceinline__ void emit_node(int p, const SweepConsts<V> &c, V nm, V rm, V np, V rp, Emit &emit) {
+    const V mid = vmul(c.h2, vadd(u[p + 2], u[p + 3]));
+    emit(p, vfma(nm, rm, vfma(W[p + 2], c.mh6, mid)), vfma(np, rp, vfma(W[p + 3], c.mh6, mid)));
+  }
+};
+
+// Stencil j of an arc-length segment, (X_{j+2}, Y_{j+2}, Z_{j+3}) with T_{j+2}, T_{j+3}, serves the "-"
+// side of node j and the "+" side of node j - 1 (see group_corr_v).  emit(p, dm, dp) receives node i0 + p.
+template <int K, class V, class LoadV, class Emit>
+__device__ __forceinline__ void sweep_stream(LoadV u_at, const SweepConsts<V> &c, Emit emit) {
+  Window<K + 5, V> w;
+  V qX[K + 6], qY[K + 6], qZ[K + 6];
+  FValV<V> FD[K + 6];
+
+  auto al_qX = [&](int m) {                  // interval (D2_m, R_m), R = 2 D2_m - D2_{m-1}
+    const V R = r_end(w.D2[m], w.W[m - 1]);
+    qX[m] = q_interval_v(w.D2[m], FD[m], R, f_eval_v(R), c.eps4);
+  };
+  auto al_qY = [&](int m) { qY[m] = q_interval_v(w.D2[m], FD[m], w.D2[m + 1], FD[m + 1], c.eps4); };
+  auto al_qZ = [&](int m) {                  // interval (L_m, D2_m), L = 2 D2_m - D2_{m+1}
+    const V Lv = l_end(w.D2[m], w.W[m]);
+    qZ[m] = q_interval_v(Lv, f_eval_v(Lv), w.D2[m], FD[m], c.eps4);
+  };
+
+  // ---- prologue: everything node 0 needs
+#pragma unroll
+  for (int m = 0; m <= 5; ++m) w.u[m] = u_at(m);
+#pragma unroll
+  for (int m = 1; m <= 5; ++m) w.pos(m, c);
+#pragma unroll
+  for (int m = 2; m <= 4; ++m) FD[m] = f_eval_v(w.D2[m]);
+  al_qX(2); al_qY(2); al_qZ(3);
+  al_qX(3); al_qY(3); al_qZ(4);
+
+#pragma unroll
+  for (int p = 0; p < K; ++p) {
+    V nm, rm, np, rp, unused0, unused1;
+    group_corr_v<true, true, false>(qX[p + 2], qY[p + 2], qZ[p + 3], w.Ta[p + 2], w.Tb[p + 3], w.Ta[p + 2],
+                                    w.Tb[p + 3], nm, rm, unused0, unused1);
+    group_corr_v<true, false, true>(qX[p + 3], qY[p + 3], qZ[p + 4], w.Ta[p + 3], w.Tb[p + 4], w.Ta[p + 4],
+                                    w.Tb[p + 3], unused0, unused1, np, rp);
+    w.emit_node(p, c, nm, rm, np, rp, emit);
+    // advance the window by one position
+    if (p + 1 < K) {
+      w.u[p + 6] = u_at(p + 6);
+      w.pos(p + 6, c);
+      FD[p + 5] = f_eval_v(w.D2[p + 5]);
+      al_qX(p + 4);
+      al_qY(p + 4);
+      al_qZ(p + 5);
+    }
+  }
+}
+
+// Jiang-Peng sweep, in units of the first differences: v_at(m) returns Delta^+ phi / dx at position
+// i0 - 3 + m; s_m = v_m - v_{m-1}, d_m = s_{m+1} - s_m, T_m = d_m - d_{m-1}.  Stencil j is
+// (X_{j+1}, Y_{j+2}, Z_{j+3}), the indicators of the pairs (s_m, s_{m+1}).
+template <int K, class V, class LoadV, class Emit>
+__device__ __forceinline__ void sweep_stream_jp(LoadV v_at, V eps, Emit emit) {
   V v[K + 5];
   V s[K + 5];
-  V dd[K + 5];                               // d_m = s_{m+1} - s_m
+  V dd[K + 5];
   V T[K + 5];
   V T3[K + 5];                               // T_m / 3
   V qX[K + 6], qY[K + 6], qZ[K + 6];
-  V D2[K + 6];
-  V W[K + 6];                                // W_m = d_m / dx = D2_{m+1} - D2_m up to rounding
-  FValV<V> FD[K + 6];
 
-  auto pos_s = [&](int m) {                  // s, d, and D2 and W for arc length
+  auto pos_s = [&](int m) {
     s[m] = vsub(v[m], v[m - 1]);
-    if (WEIGHTS == W_ARCLEN) D2[m] = vmul(s[m], rdx);
-    if (m >= 2) {
-      dd[m - 1] = vsub(s[m], s[m - 1]);
-      if (WEIGHTS == W_ARCLEN) W[m - 1] = vmul(dd[m - 1], rdx);
-    }
+    if (m >= 2) dd[m - 1] = vsub(s[m], s[m - 1]);
   };
   const V c13 = vsplat(1.0f / 3.0f, eps);
   auto pos_T = [&](int m) {
     T[m] = vsub(dd[m], dd[m - 1]);
     T3[m] = vmul(T[m], c13);
   };
-  auto al_qX = [&](int m) {                  // interval (D2_m, R_m), R = 2 D2_m - D2_{m-1}
-    const V R = r_end(D2[m], W[m - 1]);
-    qX[m] = q_interval_v(D2[m], FD[m], R, f_eval_v(R), eps4);
-  };
-  auto al_qY = [&](int m) { qY[m] = q_interval_v(D2[m], FD[m], D2[m + 1], FD[m + 1], eps4); };
-  auto al_qZ = [&](int m) {                  // interval (L_m, D2_m), L = 2 D2_m - D2_{m+1}
-    const V Lv = l_end(D2[m], W[m]);
-    qZ[m] = q_interval_v(Lv, f_eval_v(Lv), D2[m], FD[m], eps4);
-  };
-  auto jp_pair = [&](int m) {                // Jiang-Peng quantities of the pair (s_m, s_{m+1})
+  auto jp_pair = [&](int m) {
     const V x = s[m], y = s[m + 1];
     const V d = vsub(x, y);
     const V d13 = vmul(vsplat(13.0f, x), vmul(d, d));
-    const V a = vfma(vsplat(-3.0f, x), y, x), b = vadd(x, y), c = vsub(vmul(vsplat(3.0f, x), x), y);
+    const V a = vfma(vsplat(-3.0f, x), y, x), b = vadd(x, y), cc = vsub(vmul(vsplat(3.0f, x), x), y);
     const V three = vsplat(3.0f, x);
     const V ea = vadd(vfma(vmul(three, a), a, d13), eps), eb = vadd(vfma(vmul(three, b), b, d13), eps);
-    const V ec = vadd(vfma(vmul(three, c), c, d13), eps);
+    const V ec = vadd(vfma(vmul(three, cc), cc, d13), eps);
     qX[m] = vmul(ea, ea);
     qY[m] = vmul(eb, eb);
     qZ[m] = vmul(ec, ec);
   };
 
-  // ---- prologue: everything node 0 needs
 #pragma unroll
   for (int m = 0; m <= 5; ++m) v[m] = v_at(m);
 #pragma unroll
   for (int m = 1; m <= 5; ++m) pos_s(m);
 #pragma unroll
   for (int m = 2; m <= 4; ++m) pos_T(m);
-  if (WEIGHTS == W_ARCLEN) {
 #pragma unroll
-    for (int m = 2; m <= 4; ++m) FD[m] = f_eval_v(D2[m]);
-    al_qX(2); al_qY(2); al_qZ(3);
-    al_qX(3); al_qY(3); al_qZ(4);
-  } else {
-#pragma unroll
-    for (int m = 1; m <= 4; ++m) jp_pair(m);
-  }
+  for (int m = 1; m <= 4; ++m) jp_pair(m);
 
   const V cm16 = vsplat(-1.0f / 6.0f, eps), c12 = vsplat(0.5f, eps);
 #pragma unroll
   for (int p = 0; p < K; ++p) {
-    // node p: phi^- = (c + T_b/12) - corr^-, phi^+ = (c - T_b/12) + corr^+
     const V mid = vmul(c12, vadd(v[p + 2], v[p + 3]));
     const V tb2 = vmul(c12, T[p + 3]);
-    V nm, rm, np, rp;
-    if (WEIGHTS == W_ARCLEN) {
-      side_corr_v<true>(qX[p + 2], qY[p + 2], qZ[p + 3], T3[p + 2], tb2, nm, rm);
-      side_corr_v<false>(qZ[p + 4], qY[p + 3], qX[p + 3], T3[p + 4], tb2, np, rp);
-    } else {
-      side_corr_v<true>(qX[p + 1], qY[p + 2], qZ[p + 3], T3[p + 2], tb2, nm, rm);
-      side_corr_v<false>(qZ[p + 4], qY[p + 3], qX[p + 2], T3[p + 4], tb2, np, rp);
-    }
+    V nm, rm, np, rp, unused0, unused1;
+    group_corr_v<true, true, false>(qX[p + 1], qY[p + 2], qZ[p + 3], T3[p + 2], tb2, T3[p + 2], tb2, nm, rm,
+                                    unused0, unused1);
+    group_corr_v<true, false, true>(qX[p + 2], qY[p + 3], qZ[p + 4], T3[p + 4], tb2, T3[p + 4], tb2, unused0,
+                                    unused1, np, rp);
     emit(p, vfma(nm, rm, vfma(dd[p + 2], cm16, mid)), vfma(np, rp, vfma(dd[p + 3], cm16, mid)));
-    // advance the window by one position
     if (p + 1 < K) {
       v[p + 6] = v_at(p + 6);
       pos_s(p + 6);
       pos_T(p + 5);
-      if (WEIGHTS == W_ARCLEN) {
-        FD[p + 5] = f_eval_v(D2[p + 5]);
-        al_qX(p + 4);
-        al_qY(p + 4);
-        al_qZ(p + 5);
-      } else {
-        jp_pair(p + 5);
-      }
+      jp_pair(p + 5);
     }
   }
 }
@@ -365,15 +422,8 @@ __device__ __forceinline__ void sweep_stream(LoadV v_at, V rdx, V eps4, V eps, E
 // and after the last node).  When it returns false the emitted values, if any, are not to be
 // used and the caller sweeps the warp's segments again with sweep_stream.
 template <int K, class V, class LoadV, class Emit>
-__device__ __forceinline__ bool sweep_stream_short(LoadV v_at, V rdx, V eps4, Emit emit) {
-  using LN = Lanes<V>;
-  V v[K + 5];
-  V s[K + 5];
-  V dd[K + 5];
-  V T[K + 5];
-  V T3[K + 5];
-  V D2[K + 6];
-  V W[K + 6];
+__device__ __forceinline__ bool sweep_stream_short(LoadV u_at, const SweepConsts<V> &c, Emit emit) {
+  Window<K + 5, V> w;
   V S[K + 6];                                // S_m = sqrt(1 + D2_m^2)
   V qX[K + 6], qY[K + 6], qZ[K + 6];
   bool ok = true;
@@ -381,62 +431,48 @@ __device__ __forceinline__ bool sweep_stream_short(LoadV v_at, V rdx, V eps4, Em
   auto sq = [&](V u) { return s_eval_v(u); };   // FValV::s of f_eval_v
   auto qv = [&](V sa, V sb) {                // q of q_interval_v on its trapezoid branch
     const V ss = vadd(sa, sb);
-    const V e = vfma(ss, ss, eps4);
+    const V e = vfma(ss, ss, c.eps4);
     return vmul(e, e);
   };
-  auto pos_s = [&](int m) {
-    s[m] = vsub(v[m], v[m - 1]);
-    D2[m] = vmul(s[m], rdx);
-    if (m >= 2) {
-      dd[m - 1] = vsub(s[m], s[m - 1]);
-      W[m - 1] = vmul(dd[m - 1], rdx);
-      ok &= short_width(W[m - 1]);
-    }
+  auto pos = [&](int m) {
+    w.pos(m, c);
+    if (m >= 2) ok &= short_width(w.W[m - 1]);
   };
-  const V c13 = vsplat(1.0f / 3.0f, rdx);
-  auto pos_T = [&](int m) {
-    T[m] = vsub(dd[m], dd[m - 1]);
-    T3[m] = vmul(T[m], c13);
-  };
-  auto al_qX = [&](int m) { qX[m] = qv(S[m], sq(r_end(D2[m], W[m - 1]))); };
+  auto al_qX = [&](int m) { qX[m] = qv(S[m], sq(r_end(w.D2[m], w.W[m - 1]))); };
   auto al_qY = [&](int m) { qY[m] = qv(S[m], S[m + 1]); };
-  auto al_qZ = [&](int m) { qZ[m] = qv(sq(l_end(D2[m], W[m])), S[m]); };
-  // side_corr_v when the denominator is known to be in range (neg: r = -1 / den)
-  auto corr = [&](V q0, V q1, V q2, V ta3, V tb2, bool neg, V &num, V &rd) {
-    const V A0 = vmul(q1, q2), A1 = vmul(q0, q2), A2 = vmul(q0, q1);
-    const V den = vfma(vsplat(6.0f, q0), A1, vfma(vsplat(3.0f, q0), A2, A0));
-    num = vfma(A0, ta3, vmul(A2, tb2));
-#pragma unroll
-    for (int i = 0; i < LN::n; ++i) LN::at(rd, i) = sfu_rcp(neg ? -LN::get(den, i) : LN::get(den, i));
+  auto al_qZ = [&](int m) { qZ[m] = qv(sq(l_end(w.D2[m], w.W[m])), S[m]); };
+  // the denominators stay in range on short segments: no check
+  auto stencil = [&](int j, auto minus_c, auto plus_c, V &nm, V &rm, V &np, V &rp) {
+    constexpr bool MI = decltype(minus_c)::value, PL = decltype(plus_c)::value;
+    group_corr_v<false, MI, PL>(qX[j + 2], qY[j + 2], qZ[j + 3], w.Ta[j + 2], w.Tb[j + 3], w.Ta[j + 3],
+                                w.Tb[j + 2], nm, rm, np, rp);
   };
 
 #pragma unroll
-  for (int m = 0; m <= 5; ++m) v[m] = v_at(m);
+  for (int m = 0; m <= 5; ++m) w.u[m] = u_at(m);
 #pragma unroll
-  for (int m = 1; m <= 5; ++m) pos_s(m);
+  for (int m = 1; m <= 5; ++m) pos(m);
 #pragma unroll
-  for (int m = 2; m <= 4; ++m) pos_T(m);
-#pragma unroll
-  for (int m = 2; m <= 4; ++m) S[m] = sq(D2[m]);
+  for (int m = 2; m <= 4; ++m) S[m] = sq(w.D2[m]);
   al_qX(2); al_qY(2); al_qZ(3);
   al_qX(3); al_qY(3); al_qZ(4);
-  ok &= short_sizes(D2[2], eps4);
+  ok &= short_sizes(w.D2[2], c.eps4);
   if (!__all_sync(0xffffffffu, ok)) return false;
 
-  const V cm16 = vsplat(-1.0f / 6.0f, rdx), c12 = vsplat(0.5f, rdx);
+  V nm, rm, dummy0, dummy1;
+  stencil(0, std::true_type{}, std::false_type{}, nm, rm, dummy0, dummy1);
 #pragma unroll
   for (int p = 0; p < K; ++p) {
-    const V mid = vmul(c12, vadd(v[p + 2], v[p + 3]));
-    const V tb2 = vmul(c12, T[p + 3]);
-    V nm, rm, np, rp;
-    corr(qX[p + 2], qY[p + 2], qZ[p + 3], T3[p + 2], tb2, true, nm, rm);
-    corr(qZ[p + 4], qY[p + 3], qX[p + 3], T3[p + 4], tb2, false, np, rp);
-    emit(p, vfma(nm, rm, vfma(dd[p + 2], cm16, mid)), vfma(np, rp, vfma(dd[p + 3], cm16, mid)));
+    V nm1, rm1, np, rp;
+    if (p + 1 < K) stencil(p + 1, std::true_type{}, std::true_type{}, nm1, rm1, np, rp);
+    else stencil(p + 1, std::false_type{}, std::true_type{}, nm1, rm1, np, rp);
+    w.emit_node(p, c, nm, rm, np, rp, emit);
+    nm = nm1;
+    rm = rm1;
     if (p + 1 < K) {
-      v[p + 6] = v_at(p + 6);
-      pos_s(p + 6);
-      pos_T(p + 5);
-      S[p + 5] = sq(D2[p + 5]);
+      w.u[p + 6] = u_at(p + 6);
+      pos(p + 6);
+      S[p + 5] = sq(w.D2[p + 5]);
       al_qX(p + 4);
       al_qY(p + 4);
       al_qZ(p + 5);
