@@ -733,6 +733,9 @@ def run_ours(args):
         roof["issue"] = {"achieved_tinst_s": achieved, "peak_tinst_s": peak, "frac": achieved / peak,
                          "peak_source": f"derived: {SM_COUNT} SMs x 4 schedulers x 32 lanes x {SM_MAX_MHZ:.0f} MHz",
                          "thread_instructions_per_point_stage": inst}
+        if traffic.get("counters"):
+            # issue slots, resident warps and pipe activity of the same launches (one-pass ncu counters)
+            roof["ncu_counters"] = {k: v for k, v in traffic["counters"].items() if k != "note"}
     cpu = None
     if not args.no_cpu and ws >= 1:
         import oracle

@@ -92,6 +92,37 @@ __global__ void ghosts_pair(float *hi_, float *lo_, const DevState *st, float *c
   lo[q] = l;
 }
 
+// MIXED increment array e of a stage state phi_k = hi + e (hi = the high part of phi^n, whose ghost frame is
+// already in place): the ghost of phi_k is formed in double from the interior values of hi + e and stored as
+// e_ghost = ghost - hi_ghost, so that hi + e holds the extrapolated phi_k at every ghost cell (extrapolating
+// e alone would leave the difference between hi's own extrapolation and hi's ghost, which carries the split
+// of phi^n's ghost into hi and lo, in the ghost values).
+__global__ void ghosts_incr(float *e, const DevState *st, const float *hi0, const float *hi1, int nx, int ny,
+                            int pitch, int dim, int bc) {
+  const float *hi = st->cur ? hi1 : hi0;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nrow = ny * 6, ncol = (dim == 2) ? nx * 6 : 0;
+  double v;
+  size_t q;
+  if (t < nrow) {
+    const int j = t / 6, k = t % 6;
+    const int g = (k < 3) ? -(k + 1) : nx + (k - 3);
+    auto get = [&](int ii) { const size_t r = pidx(ii, j, pitch, dim); return (double)hi[r] + (double)e[r]; };
+    v = ghost_value<double>(g, nx, bc, get);
+    q = pidx(g, j, pitch, dim);
+  } else if (t < nrow + ncol) {
+    const int u = t - nrow;
+    const int i = u / 6, k = u % 6;
+    const int g = (k < 3) ? -(k + 1) : ny + (k - 3);
+    auto get = [&](int jj) { const size_t r = pidx(i, jj, pitch, dim); return (double)hi[r] + (double)e[r]; };
+    v = ghost_value<double>(g, ny, bc, get);
+    q = pidx(i, g, pitch, dim);
+  } else {
+    return;
+  }
+  e[q] = (float)(v - (double)hi[q]);
+}
+
 template <typename Src, typename Dst>
 __global__ void pack_kernel(const Src *pad, Dst *dst, int nx, int ny, int pitch, int dim) {
   const size_t n = (size_t)nx * ny;
@@ -128,9 +159,8 @@ __global__ void join_kernel(const float *hi, const float *lo, const float *delta
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
     const int j = (int)(k / nx), i = (int)(k % nx);
     const size_t q = pidx(i, j, pitch, dim);
-    double v = (double)hi[q] + (double)lo[q];
-    if (delta) v += (double)delta[q];
-    dst[k] = v;
+    // phi^n = hi + lo; a MIXED stage state is hi + its increment array (which holds the low part)
+    dst[k] = (double)hi[q] + (double)(delta ? delta[q] : lo[q]);
   }
 }
 
@@ -152,6 +182,11 @@ int launch_ghosts(const GhostParams &g, void *stream) {
                                           nullptr, nullptr, g.nx, g.ny, g.pitch, g.dim, g.bc,
                                           reinterpret_cast<float *>(g.mix_hi[0]), reinterpret_cast<float *>(g.mix_lo[0]),
                                           reinterpret_cast<float *>(g.mix_hi[1]), reinterpret_cast<float *>(g.mix_lo[1]));
+  } else if (g.prec == P_MIXED) {
+    ghosts_incr<<<blocks, kBlock, 0, s>>>(reinterpret_cast<float *>(g.a0), g.state,
+                                          reinterpret_cast<const float *>(g.mix_hi[0]),
+                                          reinterpret_cast<const float *>(g.mix_hi[1]), g.nx, g.ny, g.pitch, g.dim,
+                                          g.bc);
   } else if (g.prec == P_F64) {
     ghosts_plain<double><<<blocks, kBlock, 0, s>>>(reinterpret_cast<double *>(g.a0), g.nx, g.ny, g.pitch, g.dim, g.bc);
   } else {

@@ -58,9 +58,9 @@ struct StageParams {
 
 struct GhostParams {
   int nx, ny, pitch, dim, bc, prec;
-  void *a0, *a1;        // arrays to fill (F64/F32: a0; MIXED hi/lo pair: a0, a1, or delta: a0 only)
-  int mixed_pair;       // MIXED: 1 if (a0, a1) is a hi/lo pair, 0 if a0 is a delta array
-  DevState *state;      // MIXED hi/lo: the pair is mix_*[cur] when non-null
+  void *a0, *a1;        // arrays to fill (F64/F32: a0; MIXED hi/lo pair: a0, a1, or increment: a0 only)
+  int mixed_pair;       // MIXED: 1 if (a0, a1) is a hi/lo pair, 0 if a0 is an increment array
+  DevState *state;      // MIXED: the pair is mix_*[cur] when non-null; an increment's high part is mix_hi[cur]
   void *mix_hi[2], *mix_lo[2];
 };
 

@@ -285,6 +285,9 @@ GhostParams ghost_params(const alw_solver *s, int after_stage) {
     if (after_stage == 1 || after_stage == 2) {
       g.a0 = after_stage == 1 ? s->D1 : s->D2;
       g.mixed_pair = 0;
+      g.state = s->st;
+      g.mix_hi[0] = s->H[0];
+      g.mix_hi[1] = s->H[1];
     } else {
       g.mixed_pair = 1;
       g.state = s->st;

@@ -94,16 +94,19 @@ __global__ void __launch_bounds__(Shape<PREC, DIM, SMALL>::NT) stage_kernel(cons
     s_a[idx] = ga[g];
     if (PREC == P_MIXED) {
       s_b[idx] = gb[g];
-      s_c[idx] = gc ? gc[g] : S(0);
+      if (gc) s_c[idx] = gc[g];
     }
   }
+  // MIXED: the stage's input is hi + X, X = the low part of phi^n (stage 1) or the increment array of the
+  // previous stage, which holds the low part as well (stages 2 and 3; see finish_node)
+  const S *s_x = gc ? s_c : s_b;
   __syncthreads();
 
   const C dx = C(p.dx), rdx = C(p.rdx), eps = C(p.eps);
   // Delta^+ phi between smem cells i0 and i1 (same row or column)
   auto diff = [&](int i0, int i1, C rd) -> C {
     if (PREC == P_MIXED) {
-      return ((s_a[i1] - s_a[i0]) + ((s_b[i1] - s_b[i0]) + (s_c[i1] - s_c[i0]))) * rd;
+      return ((s_a[i1] - s_a[i0]) + (s_x[i1] - s_x[i0])) * rd;
     } else {
       return C(s_a[i1] - s_a[i0]) * rd;
     }
@@ -128,14 +131,17 @@ __global__ void __launch_bounds__(Shape<PREC, DIM, SMALL>::NT) stage_kernel(cons
     const C L = -((H - aX * C(0.5) * (up - um)) - aY * C(0.5) * (vp - vm));
     const int sidx = ((DIM == 2) ? lyn + 3 : 0) * SW + lxn + 4;
     if (PREC == P_MIXED) {
+      // phi^n = hi + lo and phi_k = hi + e_k with e_k = lo + (phi_k - phi^n):
+      //   e_1 = lo + dt L,  e_2 = 3/4 lo + 1/4 (e_1 + dt L),  phi^{n+1} = hi + lo + 2/3 (e_2 + dt L - lo)
       const float dL = float(dt) * float(L);
+      const float lo = float(s_b[sidx]);
       if (p.stage == 1) {
-        store_node<float, DIM>(reinterpret_cast<float *>(p.out0), p.pitch, p.nx, p.ny, p.bc, gi, gj, dL);
+        store_node<float, DIM>(reinterpret_cast<float *>(p.out0), p.pitch, p.nx, p.ny, p.bc, gi, gj, lo + dL);
       } else if (p.stage == 2) {
-        const float d = 0.25f * (float(s_c[sidx]) + dL);
+        const float d = fmaf(0.75f, lo, 0.25f * (float(s_c[sidx]) + dL));
         store_node<float, DIM>(reinterpret_cast<float *>(p.out0), p.pitch, p.nx, p.ny, p.bc, gi, gj, d);
       } else {
-        const float d = (2.0f / 3.0f) * (float(s_c[sidx]) + dL);
+        const float d = (2.0f / 3.0f) * ((float(s_c[sidx]) + dL) - lo);
         float h, l;
         df_add(float(s_a[sidx]), float(s_b[sidx]), d, h, l);
         store_node<float, DIM>(reinterpret_cast<float *>(p.mix_hi[cur ^ 1]), p.pitch, p.nx, p.ny, p.bc, gi, gj, h);

@@ -349,14 +349,6 @@ __global__ void __launch_bounds__(Geo2D<TXv>::NT, Geo2D<TXv>::MINB)
     s_info[1].inst = -1;
     if ((int)blockIdx.x < ntiles) prepare(blockIdx.x, batch ? prm.tiles[blockIdx.x] : 0, 0);
   }
-  if (PREC == P_MIXED && prm.map_c < 0) {
-    // no delta array in this stage: the y sweep reads the delta slots all the same, so they hold zeros
-    // (no load ever writes them)
-    for (int i = tid; i < ARR; i += NT) {
-      raw[2 * ARR + i] = 0.0f;
-      raw[NARR * ARR + 2 * ARR + i] = 0.0f;
-    }
-  }
   __syncthreads();
 
   uint32_t phase = 0;  // bit b: parity of the next completion of bars[b]
@@ -401,21 +393,18 @@ __global__ void __launch_bounds__(Geo2D<TXv>::NT, Geo2D<TXv>::MINB)
     const float *A = raw + buf * NARR * ARR;
     const float *B = A + ARR;
     const float *C = A + 2 * ARR;
-    const bool has_delta = PREC == P_MIXED && prm.map_c >= 0;
+    // MIXED: the stage's input is A + X, the high part of phi^n plus X = its low part (stage 1) or the
+    // increment array of the previous stage, which holds the low part as well (stages 2 and 3; see the
+    // finish loop)
+    const float *X = (PREC == P_MIXED && prm.map_c >= 0) ? C : B;
 
     // ---- 1. x differences in the units of the sweep (arc length: Delta^+ phi / dx^2; Jiang-Peng:
-    // Delta^+ phi / dx), rows by warp, columns by lane (no division, conflict-free); the MIXED variant
-    // without a delta array (stage 1) is a separate loop, so that it reads two arrays, not three
+    // Delta^+ phi / dx), rows by warp, columns by lane (no division, conflict-free)
     const float rdx2 = (W == W_ARCLEN) ? d.rdx * d.rdx : d.rdx;
-    auto diff_pass = [&](auto with_delta) {
-      constexpr bool WD = decltype(with_delta)::value;
+    {
       auto cell_diff = [&](int i0, int i1) -> float {
-        if (PREC == P_MIXED) {
-          if (WD) return (A[i1] - A[i0]) + ((B[i1] - B[i0]) + (C[i1] - C[i0]));
-          return (A[i1] - A[i0]) + (B[i1] - B[i0]);
-        } else {
-          return A[i1] - A[i0];
-        }
+        if (PREC == P_MIXED) return (A[i1] - A[i0]) + (X[i1] - X[i0]);
+        return A[i1] - A[i0];
       };
       // the first TX cells of every row by whole warps, the last DXW - TX cells of all rows together
       // (a third pass per row would keep only 5 of 32 lanes busy)
@@ -432,9 +421,7 @@ __global__ void __launch_bounds__(Geo2D<TXv>::NT, Geo2D<TXv>::MINB)
         const int i0 = (r + 3) * SW + c + 1;
         dX[r * DXP + c] = cell_diff(i0, i0 + 1) * rdx2;
       }
-    };
-    if (has_delta) diff_pass(std::true_type{});
-    else diff_pass(std::false_type{});
+    }
     if (__syncthreads_or(!ok)) {
       // a tile load never completed (the differences pass above ran on whatever the buffer held):
       // flag the instance and stop; the next tile's load is issued only after this barrier, so no
@@ -461,20 +448,16 @@ __global__ void __launch_bounds__(Geo2D<TXv>::NT, Geo2D<TXv>::MINB)
       const int iy = (K * segY) * SW + colY + 4;
       const float rdy2 = (W == W_ARCLEN) ? d.rdy * d.rdy : d.rdy;
       auto make_vat = [&]() {
-        float pa = A[iy], pb = 0.0f, pc = 0.0f;
-        if (PREC == P_MIXED) {
-          pb = B[iy];
-          pc = C[iy];
-        }
+        float pa = A[iy], px = 0.0f;
+        if (PREC == P_MIXED) px = X[iy];
         return [=](int m) mutable {
           const int i1 = iy + (m + 1) * SW;
           float dy;
           if (PREC == P_MIXED) {
-            const float a1 = A[i1], b1 = B[i1], c1 = C[i1];
-            dy = (a1 - pa) + ((b1 - pb) + (c1 - pc));
+            const float a1 = A[i1], x1 = X[i1];
+            dy = (a1 - pa) + (x1 - px);
             pa = a1;
-            pb = b1;
-            pc = c1;
+            px = x1;
           } else {
             const float a1 = A[i1];
             dy = a1 - pa;
@@ -538,8 +521,12 @@ __global__ void __launch_bounds__(Geo2D<TXv>::NT, Geo2D<TXv>::MINB)
         const int sidx = (y + 3) * SW + colY + 4;
         const size_t g = rbase + (size_t)(gj + GY) * p.pitch + gi + GX;
         if (PREC == P_MIXED) {
+          // phi^n = hi + lo (A, B) and the stage states phi_1 = hi + e_1, phi_2 = hi + e_2, where the
+          // increment arrays e_k = lo + (phi_k - phi^n) carry the low part (C = e_{k-1}):
+          //   e_1 = lo + dt L,  e_2 = 3/4 lo + 1/4 (e_1 + dt L),  phi^{n+1} = hi + lo + 2/3 (e_2 + dt L - lo)
+          // (Step 5's combinations with phi_k - phi^n = e_k - lo)
           if (ST == 3) {
-            const float dd = (2.0f / 3.0f) * fmaf(dtf, L, C[sidx]);
+            const float dd = (2.0f / 3.0f) * (fmaf(dtf, L, C[sidx]) - B[sidx]);
             float h, l;
             df_add(A[sidx], B[sidx], dd, h, l);
             float *oh = reinterpret_cast<float *>(p.mix_hi[i_cur ^ 1]);
@@ -552,7 +539,7 @@ __global__ void __launch_bounds__(Geo2D<TXv>::NT, Geo2D<TXv>::MINB)
               ol[g] = l;
             }
           } else {
-            const float dd = (ST == 1) ? dtf * L : 0.25f * fmaf(dtf, L, C[sidx]);
+            const float dd = (ST == 1) ? fmaf(dtf, L, B[sidx]) : fmaf(0.75f, B[sidx], 0.25f * fmaf(dtf, L, C[sidx]));
             float *o = reinterpret_cast<float *>(p.out0);
             if (EDGE) store_node<float, 2>(o + rbase, p.pitch, nx, ny, d.bc, gi, gj, dd);
             else o[g] = dd;

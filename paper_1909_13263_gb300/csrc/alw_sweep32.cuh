@@ -24,20 +24,24 @@
 //   phi^+ = (c - T_b/12) + (A0' T_c / 3 + A2' T_b / 2) / den'.
 // The central parts are formed from d_m = s_{m+1} - s_m (s_m = v_m - v_{m-1}): for the node between
 // v_2 and v_3 of its window, c + T_b/12 = (v_2 + v_3)/2 - d_2/6 and c - T_b/12 = (v_2 + v_3)/2 - d_3/6,
-// and T_m = d_m - d_{m-1}; the widths d_m / dx are those of the arc-length intervals.
+// and T_m = d_m - d_{m-1}; the widths d_m / dx are those of the arc-length intervals.  The arc-length
+// sweeps take their input as u = v / dx (the differences pass scales by 1/dx^2), so that the second
+// differences D2_m = u_m - u_{m-1} and the widths W_m = D2_{m+1} - D2_m = d_m / dx come without a
+// multiply; dx enters once, in the constants dx/2, dx/3, -dx/6 of the central parts and of T_a/3, T_b/2.
+// The Jiang-Peng sweep needs no D2 and keeps v.
 //
 // Short intervals.  The interval mean G takes the trapezoid value (s_a + s_b) / 2 whenever the
 // interval [a, b] is short against its end values (|b - a| <= (s_a + s_b) / 64, s = sqrt(1 + u^2)).
 // On smooth data at fine grids every interval of a segment is that short (its width is a third
 // difference of phi over dx^2, about phi_xxx dx), and then F, its logarithm and the interval
 // reciprocals are never used.  sweep_stream_short computes only what the trapezoid branch needs
-// and reports whether the segment qualifies: every width W_m = d_m / dx of the segment at most
-// kShortH (which implies the trapezoid branch for all three interval kinds, because D2_{m+1} - D2_m,
-// R_m - D2_m and D2_m - L_m all equal such a width up to the rounding of D2, R or L -- below 1e-4
+// and reports whether the segment qualifies: every width W_m of the segment at most
+// kShortH (which implies the trapezoid branch for all three interval kinds, because D2_{m+1} - D2_m
+// is such a width and R_m - D2_m and D2_m - L_m equal one up to the rounding of R or L -- below 1e-4
 // while |D2| <= kShortD2, against the margin 1/32 - kShortH -- and s >= 1), |D2| at the segment
 // start at most kShortD2 and eps4 at most kShortEps4 (together
-// these keep every weight denominator below 1e29, so the overflow branch of side_corr_v cannot be
-// taken).  When the segment qualifies, both sweeps evaluate the same formulas on the same branches;
+// these keep every weight denominator below 1e29, so the overflow branch of group_corr_v is not
+// needed).  When the segment qualifies, both sweeps evaluate the same formulas on the same branches;
 // their results agree to rounding (the compiler may select instructions for the two code paths
 // differently), and the stage kernel decides between them from the segment's own data only.
 #pragma once
@@ -187,7 +191,7 @@ __device__ __forceinline__ V q_interval_v(V a, FValV<V> fa, V b, FValV<V> fb, V 
   return vmul(e, e);
 }
 
-// Slow path of side_corr_v for one lane, when the q products leave the safe float range
+// Slow path of group_corr_v for one lane, when the q products leave the safe float range
 // (kept out of line: it is rare and would otherwise be inlined at every node).
 static __device__ __noinline__ float side_corr_wide(float q0, float q1, float q2, float ta3, float tb2) {
   const float a0 = __fdividef(0.1f, q0), a1 = __fdividef(0.6f, q1), a2 = __fdividef(0.3f, q2);
