@@ -110,6 +110,7 @@ def test_fp64_solve_matches_oracle(case):
     Case(2, 150, 70, "negcos2d", bc="linextrap"),
     Case(2, 65, 33, "sin2d", alpha_mode="local_lagged"),
     Case(1, 300, 1, "burgers1d", alpha_mode="local_lagged"),
+    Case(1, 257, 1, "advect1d", bc="linextrap", alpha_mode="global_lagged"),
     Case(2, 130, 70, "optctrl2d", lo=-math.pi, hi=math.pi),
     Case(2, 70, 66, "optctrl2d", lo=-math.pi, hi=math.pi, alpha_mode="local_lagged"),
     Case(2, 97, 45, "eikonal2d", lo=0.0, hi=1.0),
