@@ -100,7 +100,8 @@ enum { ALW_DT_CFL = 0, ALW_DT_DX53 = 1 };
 /* Arithmetic.  FP64: all in double.  FP32: phi and all arithmetic in float.
  * MIXED: stencil arithmetic in float; phi^n is held as an unevaluated sum of
  * two floats (hi + lo, about 48 significant bits) and the RK stages store
- * float increments phi_s - phi^n, so the accumulation of phi over long runs
+ * float increments that carry the low part, lo + (phi_s - phi^n), so a stage
+ * state is hi plus one float array and the accumulation of phi over long runs
  * keeps double-class precision; the CFL reduction is in double.  In FP32 and
  * MIXED the square roots, logarithms, reciprocals, sines and cosines of the
  * stencil and of the Hamiltonians are the GPU's hardware approximations

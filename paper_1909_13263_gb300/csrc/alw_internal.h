@@ -49,9 +49,9 @@ struct StageParams {
   double dt_value;       // LOOP_STAGE: the dt of this stage
   int small_tiles;       // FP64 2D: 0 default tiles; 16 x 16 tiles with 4-node (1) or 2-node (2) segments
   // buffers: padded arrays whose interior origin is at row GY, column GX
-  const void *src0, *src1, *src2;  // stencil source (F64/F32: src0; MIXED: hi, lo, delta or null)
+  const void *src0, *src1, *src2;  // stencil source (F64/F32: src0; MIXED: hi, lo, previous increment or null)
   const void *base0, *base1;       // phi^n at the node (F64/F32: base0; MIXED: hi, lo; stage>=2)
-  void *out0, *out1;               // outputs (F64/F32: out0; MIXED: delta, or hi/lo at stage 3)
+  void *out0, *out1;               // outputs (F64/F32: out0; MIXED: increment, or hi/lo at stage 3)
   void *mix_hi[2], *mix_lo[2];     // MIXED: the two phi^n buffer pairs (selected by DevState::cur)
   DevState *state;
 };

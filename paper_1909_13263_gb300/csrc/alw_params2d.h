@@ -27,7 +27,7 @@ struct Stage2DParams {
   CUtensorMap maps[6];  // FP32: 0 = phi^n, 1 = stage-1 state, 2 = stage-2 state;
                         // MIXED: 0/1 = hi pairs, 2/3 = lo pairs, 4 = delta_1, 5 = delta_2
   StageParams p;        // stage, modes, slots, pitch and buffers (per-instance fields unused in a batch)
-  int map_a, map_b, map_c;  // FP32: source, base (-1: none); MIXED: hi base index, lo base index, delta (-1: none)
+  int map_a, map_b, map_c;  // FP32: source, base (-1: none); MIXED: hi base index, lo base index, previous increment (-1: none)
   int ntiles;               // work-list length
   int grid_ctas;            // persistent CTAs to launch (0: as many as fit; never more than fit or ntiles)
   int tile_w;               // tile width: 64 (0 means 64) or 32; the maps' boxes and insts[].tiles_x match it

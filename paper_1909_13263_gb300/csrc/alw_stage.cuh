@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(Shape<PREC, DIM, SMALL>::NT) stage_kernel(cons
   extern __shared__ __align__(16) unsigned char smem_raw[];
   S *s_a = reinterpret_cast<S *>(smem_raw);            // phi (or hi)
   S *s_b = s_a + SH * SW;                               // lo (MIXED)
-  S *s_c = s_b + SH * SW;                               // delta (MIXED)
+  S *s_c = s_b + SH * SW;                               // previous stage's increment (MIXED)
   C *s_u = reinterpret_cast<C *>(smem_raw + (size_t)Sh::NARR * SH * SW * sizeof(S));
   __shared__ double s_red[2][NT / 32];
   __shared__ int s_last;

@@ -8,7 +8,8 @@
 // of a double buffer on an mbarrier -- while all threads compute the current
 // tile:
 //   1. differences pass: Delta^+ phi along x (dX) for every cell, combining
-//      the MIXED parts (hi + lo + delta) once per cell;
+//      the two MIXED parts (hi + lo, or hi + the previous stage's increment
+//      array, which carries lo) once per cell;
 //   2. both sweeps in one pass, packed two lanes per value (f32x2): each
 //      thread sweeps nodes 8w..8w+7 of row `lane` along x (warp w; the odd dX
 //      pitch makes these column-wise reads conflict-free) in lane .x and 8
