@@ -61,13 +61,15 @@ STAGE2D_SOURCES = ("alw_stage2d_mixed.cu", "alw_stage2d_f32.cu", "alw_launch2d.c
 
 
 def _kernel_source_hash() -> str:
-    """Hash of the stage kernel's sources with `//` comments and blank lines removed (a comment edit
-    does not change the kernel the traffic record was taken on)."""
+    """Hash of the stage kernel's sources with `//` comments, blank lines and diagnostic pragmas removed
+    (an edit of those does not change the kernel the traffic record was taken on)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1909_13263_gb300", "csrc")
     for f in STAGE2D_SOURCES:
         for line in open(os.path.join(csrc, f), encoding="utf-8"):
             code = line.split("//", 1)[0].rstrip()
+            if code.lstrip().startswith(("#pragma nv_diagnostic", "#pragma nv_diag_suppress")):
+                continue
             if code:
                 h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]

@@ -49,6 +49,12 @@
 
 #include "alw_device.cuh"
 
+// The sweeps' window arrays are filled position by position after the lambdas that read them are defined;
+// the front end's "used before its value is set" (549) fires at each such capture although every element
+// is written before it is read.
+#pragma nv_diagnostic push
+#pragma nv_diag_suppress 549
+
 namespace alw {
 
 constexpr float kShortH = 0.03f;      // largest width D2_{m+1} - D2_m of a short segment
@@ -486,3 +492,5 @@ __device__ __forceinline__ bool sweep_stream_short(LoadV u_at, const SweepConsts
 }
 
 }  // namespace alw
+
+#pragma nv_diagnostic pop
