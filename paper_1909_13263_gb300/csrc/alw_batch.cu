@@ -509,8 +509,6 @@ alw_status autotune(alw_batch *b) {
     }
   }
   std::vector<char> live(b->h_inst.size(), 1);
-  alw_batch_tuning best{};
-  double best_ms = 1e30;
   const int widths[2] = {kTile2DX, kTile2DXNarrow};
   const int orders[3] = {ALW_ORDER_INSTANCE, ALW_ORDER_LARGEST_FIRST, ALW_ORDER_INTERLEAVED};
   // one launch per stage is a choice only when the batch mixes Hamiltonians
@@ -523,30 +521,60 @@ alw_status autotune(alw_batch *b) {
   // stages, so the run length is fixed rather than tuned)
   const int runs[1] = {kDefaultRun};
   b->tuning.grid_ctas = 0;
+  // successive halving: every candidate is timed once (after one warm-up pass per kernel form, which
+  // also loads the form's kernels), the three fastest once more; the best two-pass total wins
+  struct Cand {
+    alw_batch_tuning t;
+    double ms;
+  };
+  std::vector<Cand> cands;
+  auto time_one = [&](const alw_batch_tuning &t, int passes, double *ms) -> alw_status {
+    b->tuning.tile_w = t.tile_w;
+    b->tuning.one_launch = t.one_launch;
+    b->grid_cap = cap_for(b);
+    alw_status st = upload_groups(b, live, t.order, t.run, nullptr);
+    if (st) return st;
+    return trial(b, passes, ms);
+  };
   for (int one = 0; one < launches_n; ++one)
     for (int w : widths) {
       b->tuning.tile_w = w;
       b->tuning.one_launch = one;
       b->grid_cap = cap_for(b);
       if (b->grid_cap <= 0) continue;
+      bool warm = false;
       for (int o : orders)
         for (int l : runs) {
-          alw_status st = upload_groups(b, live, o, l, nullptr);
-          if (st) return st;
+          alw_batch_tuning t{};
+          t.order = o;
+          t.run = l;
+          t.tile_w = w;
+          t.one_launch = one;
           double ms;
-          st = trial(b, 1, &ms);  // warm-up
-          if (st) return st;
-          st = trial(b, 3, &ms);
-          if (st) return st;
-          if (ms < best_ms) {
-            best_ms = ms;
-            best.order = o;
-            best.run = l;
-            best.tile_w = w;
-            best.one_launch = one;
+          alw_status st;
+          if (!warm) {
+            st = time_one(t, 1, &ms);
+            if (st) return st;
+            warm = true;
           }
+          st = time_one(t, 1, &ms);
+          if (st) return st;
+          cands.push_back({t, ms});
         }
     }
+  if (cands.empty()) return berr(ALW_ECUDA, "stage kernel occupancy query failed");
+  std::sort(cands.begin(), cands.end(), [](const Cand &x, const Cand &y) { return x.ms < y.ms; });
+  alw_batch_tuning best = cands[0].t;
+  double best_ms = 1e30;
+  for (size_t i = 0; i < cands.size() && i < 3; ++i) {
+    double ms;
+    alw_status st = time_one(cands[i].t, 1, &ms);
+    if (st) return st;
+    if (ms + cands[i].ms < best_ms) {
+      best_ms = ms + cands[i].ms;
+      best = cands[i].t;
+    }
+  }
   best.steps_per_graph = total >= 4096 ? 2 : (total >= 512 ? 8 : 32);
   best.grid_ctas = 0;  // occupancy cap
   b->tuning = best;
