@@ -144,6 +144,44 @@ def test_full_size_8192_sampled_stage_parity(precision, alpha):
     assert err <= tol, err
 
 
+def test_large_ragged_linextrap_three_stages_sampled():
+    # a large non-square grid with ragged tiles in both directions (12347 = 192 * 64 + 59 columns, 5003 =
+    # 156 * 32 + 11 rows), dx != dy and linear-extrapolation ghosts (Example 10's Hamiltonian and data): every
+    # stage of the MIXED path at sampled nodes -- the boundary bands, the ragged last tiles, tile seams and
+    # random interior nodes -- against the oracle's per-node operator applied to the GPU's previous stage
+    # state (stage 2 and 3 each checked on their own input)
+    nx, ny = 12347, 5003
+    case = Case(2, nx, ny, "sin2d", bc="linextrap", lo=-1.0, hi=1.0, precision="mixed", alpha_mode="fixed",
+                alpha_fixed=(1.0, 1.0))
+    x, dx = inputs.axis(nx, -1.0, 1.0, "linextrap")
+    y, dy = inputs.axis(ny, -1.0, 1.0, "linextrap")
+    phi0 = np.ascontiguousarray(inputs.phi0_riemann_2d(x, y))
+    dt = 0.6 / (1.0 / dx + 1.0 / dy)
+    with case.solver() as s:
+        s.set_phi0(phi0)
+        got = []
+        for stage in (1, 2, 3):
+            s.run_stage(stage, dt)
+            got.append(s.get_stage_phi(stage) if stage < 3 else s.get_phi())
+    rng = np.random.default_rng(12347)
+    pts = [(0, 0), (nx - 1, ny - 1), (0, ny - 1), (nx - 1, 0), (1, 2), (2, 1), (nx - 2, ny - 3), (nx - 3, ny - 2),
+           (63, 31), (64, 32), (12287, 4991), (12288, 4992), (nx // 2, ny // 2), (nx // 2 + 1, ny // 2 - 1)]
+    pts += [(int(i), int(j)) for i, j in zip(rng.integers(0, nx, 300), rng.integers(0, ny, 300))]
+    pts += [(int(i), int(j)) for i, j in zip(rng.integers(0, 3, 60), rng.integers(0, ny, 60))]
+    pts += [(int(i), int(j)) for i, j in zip(rng.integers(0, nx, 60), rng.integers(ny - 3, ny, 60))]
+    cfg = case.cfg()
+    a = np.array(case.alpha_fixed)
+    p1, p2, p3 = (np.ascontiguousarray(g, dtype=np.float64) for g in got)
+    errs = [0.0, 0.0, 0.0]
+    for i, j in pts:
+        r1 = phi0[j, i] + dt * oracle.point_L(cfg, phi0, i, j, a)
+        r2 = 0.75 * phi0[j, i] + 0.25 * (p1[j, i] + dt * oracle.point_L(cfg, p1, i, j, a))
+        r3 = phi0[j, i] / 3.0 + 2.0 * (p2[j, i] + dt * oracle.point_L(cfg, p2, i, j, a)) / 3.0
+        errs = [max(errs[0], abs(p1[j, i] - r1)), max(errs[1], abs(p2[j, i] - r2)), max(errs[2], abs(p3[j, i] - r3))]
+    tol = 64 * 2.0**-24 * np.abs(phi0).max()
+    assert max(errs) <= tol, (errs, tol)
+
+
 def _patch_stages(phi0, i, j, dx, dt, alpha, weights):
     """The oracle's phi_1 on the 13 x 13 nodes, phi_2 on the 7 x 7 nodes and phi^{n+1} at the node
     around (i, j) of one RK3 step (Step 5) with the flux alpha `alpha` in every stage, from a 19 x 19
