@@ -912,7 +912,7 @@ def main():
                     help="paths of the precision report's Example 3 rows (Example 10 always runs all three)")
     ap.add_argument("--report-ex10-sizes", type=str, default="1024",
                     help="precision report: grid sides of Example 10 (comma-separated)")
-    ap.add_argument("--serve-count", type=int, default=200)
+    ap.add_argument("--serve-count", type=int, default=400)
     ap.add_argument("--serve-budget-gb", type=float, default=60.0)
     args = ap.parse_args()
     if args.warmup < 3:
