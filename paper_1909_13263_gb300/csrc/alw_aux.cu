@@ -183,6 +183,8 @@ int launch_ghosts(const GhostParams &g, void *stream) {
                                           reinterpret_cast<float *>(g.mix_hi[0]), reinterpret_cast<float *>(g.mix_lo[0]),
                                           reinterpret_cast<float *>(g.mix_hi[1]), reinterpret_cast<float *>(g.mix_lo[1]));
   } else if (g.prec == P_MIXED) {
+    // an increment's ghosts are formed against the current high part, whose buffer the state names
+    if (!g.state || !g.mix_hi[0] || !g.mix_hi[1]) return (int)cudaErrorInvalidValue;
     ghosts_incr<<<blocks, kBlock, 0, s>>>(reinterpret_cast<float *>(g.a0), g.state,
                                           reinterpret_cast<const float *>(g.mix_hi[0]),
                                           reinterpret_cast<const float *>(g.mix_hi[1]), g.nx, g.ny, g.pitch, g.dim,
