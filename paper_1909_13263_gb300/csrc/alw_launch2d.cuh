@@ -44,7 +44,11 @@ static int launch2d_h(const Stage2DParams &prm, cudaStream_t s) {
   // batches, which take the position-free Hamiltonians only)
   if (prm.insts && prm.batch_kind1 == 0) return launch2d_one<PREC, W, H_RUNTIME, TX>(prm, s);
   switch (prm.insts ? prm.batch_kind1 - 1 : prm.inst0.ham) {
-    case H_BURGERS2D: return launch2d_one<PREC, W, H_BURGERS2D, TX>(prm, s);
+    case H_BURGERS2D:
+      // a grid-wide or fixed flux alpha needs only the grid maximum of the node alphas
+      if (prm.p.alpha_mode != A_LOCAL_LAGGED && prm.p.alpha_mode != A_LOCAL_EXACT)
+        return launch2d_one<PREC, W, H_BURGERS2D_GRID, TX>(prm, s);
+      return launch2d_one<PREC, W, H_BURGERS2D, TX>(prm, s);
     case H_NEGCOS2D: return launch2d_one<PREC, W, H_NEGCOS2D, TX>(prm, s);
     case H_SIN2D: return launch2d_one<PREC, W, H_SIN2D, TX>(prm, s);
     case H_EIKONAL2D: return launch2d_one<PREC, W, H_EIKONAL2D, TX>(prm, s);

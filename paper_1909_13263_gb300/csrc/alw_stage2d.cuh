@@ -125,8 +125,13 @@ template <> struct Ham2<H_OPTCTRL2D> {
 // of several Hamiltonians in one launch: the kind of the tile's instance, dispatched per node (the
 // branch is uniform across a tile, so warps never diverge on it).
 constexpr int H_RUNTIME = -1;
+// Burgers with a grid-wide or fixed flux alpha: the finish loop does not need each node's alpha, only the
+// grid maximum, so it tracks the largest and the negated smallest corner sum without their + 1 and forms
+// max(hi + 1, -(lo + 1)) = max(|hi + 1|, |lo + 1|) once per fold (hi >= lo)
+constexpr int H_BURGERS2D_GRID = -2;
 template <int H> struct HamSel {
   static constexpr bool kSameAlpha = Ham2<H>::kSameAlpha;
+  static constexpr bool kGridFold = false;
   __device__ __forceinline__ explicit HamSel(int) {}
   __device__ __forceinline__ float value_sums(float su, float sv, float x, float y) const {
     return Ham2<H>::value_sums(su, sv, x, y);
@@ -137,8 +142,13 @@ template <int H> struct HamSel {
   }
 };
 // runtime kind: the position-free 2D Hamiltonians batches take
+template <> struct HamSel<H_BURGERS2D_GRID> : HamSel<H_BURGERS2D> {
+  static constexpr bool kGridFold = true;
+  __device__ __forceinline__ explicit HamSel(int k) : HamSel<H_BURGERS2D>(k) {}
+};
 template <> struct HamSel<H_RUNTIME> {
   static constexpr bool kSameAlpha = false;
+  static constexpr bool kGridFold = false;
   int kind;
   __device__ __forceinline__ explicit HamSel(int k) : kind(k) {}
   __device__ __forceinline__ float value_sums(float su, float sv, float x, float y) const {
@@ -355,7 +365,9 @@ __global__ void __launch_bounds__(Geo2D<TXv>::NT, Geo2D<TXv>::MINB)
   uint32_t phase = 0;  // bit b: parity of the next completion of bars[b]
   int k = 0;
   // running alpha maxima and tile count of the current run of same-instance tiles
-  float amx = 0.0f, amy = 0.0f;
+  constexpr bool GF = HamSel<H>::kGridFold;
+  constexpr float A0 = GF ? -INFINITY : 0.0f;  // identity of the running maxima
+  float amx = A0, amy = A0;
   float nfin = 0.0f;  // NaN once a non-finite L was met (see the finish loop)
   int run_tiles = 0;
   // thread 0: work-list entry of the tile after next, loaded one tile ahead of its use
@@ -391,6 +403,7 @@ __global__ void __launch_bounds__(Geo2D<TXv>::NT, Geo2D<TXv>::MINB)
     const size_t rbase = (size_t)d.row_off * p.pitch;   // element offset of the instance's rows
     const HamSel<H> ham(d.ham);
     const float dtf = s_info[buf].dtf, fax = s_info[buf].fax, fay = s_info[buf].fay;
+    const float faxh = 0.5f * fax, fayh = 0.5f * fay;
     const float *A = raw + buf * NARR * ARR;
     const float *B = A + ARR;
     const float *C = A + 2 * ARR;
@@ -506,17 +519,27 @@ __global__ void __launch_bounds__(Geo2D<TXv>::NT, Geo2D<TXv>::MINB)
         const bool inside = !EDGE || (gi < nx && gj < ny);
         const float2 u = su[y * SUP + colY];
         const float xn = fmaf((float)gi, d.dx, d.xlo), yn = fmaf((float)gj, d.dy, d.ylo);
-        float ax, ay;
-        hsel.alpha(u.x, u.y, dmq, dpq, xn, yn, ax, ay);
-        const float aX = local_alpha ? ax : fax, aY = local_alpha ? ay : fay;
         const float Hv = hsel.value_sums(u.y + u.x, dpq + dmq, xn, yn);
-        const float L = fmaf(aX * 0.5f, u.y - u.x, fmaf(aY * 0.5f, dpq - dmq, -Hv));
-        if (inside) {
-          // L depends on all four one-sided derivatives: L * 0 is NaN exactly when L is not finite
-          nfin = fmaf(L, 0.0f, nfin);
-          amx = fmaxf(amx, ax);
-          // (with a runtime Hamiltonian the fold below does not copy amx, so amy is always kept)
-          if (!HS::kSameAlpha || !HamSel<H>::kSameAlpha) amy = fmaxf(amy, ay);
+        float L;
+        if constexpr (HS::kGridFold) {
+          L = fmaf(faxh, u.y - u.x, fmaf(fayh, dpq - dmq, -Hv));
+          if (inside) {
+            nfin = fmaf(L, 0.0f, nfin);
+            amx = fmaxf(amx, fmaxf(u.x, u.y) + fmaxf(dmq, dpq));
+            amy = fmaxf(amy, -(fminf(u.x, u.y) + fminf(dmq, dpq)));
+          }
+        } else {
+          float ax, ay;
+          hsel.alpha(u.x, u.y, dmq, dpq, xn, yn, ax, ay);
+          const float aX = local_alpha ? ax : fax, aY = local_alpha ? ay : fay;
+          L = fmaf(aX * 0.5f, u.y - u.x, fmaf(aY * 0.5f, dpq - dmq, -Hv));
+          if (inside) {
+            // L depends on all four one-sided derivatives: L * 0 is NaN exactly when L is not finite
+            nfin = fmaf(L, 0.0f, nfin);
+            amx = fmaxf(amx, ax);
+            // (with a runtime Hamiltonian the fold below does not copy amx, so amy is always kept)
+            if (!HS::kSameAlpha || !HamSel<H>::kSameAlpha) amy = fmaxf(amy, ay);
+          }
         }
         if (ST == 0 || !inside) continue;
         const int sidx = (y + 3) * SW + colY + 4;
@@ -596,7 +619,12 @@ __global__ void __launch_bounds__(Geo2D<TXv>::NT, Geo2D<TXv>::MINB)
       // reaches after finishing this tile
       continue;
     }
-    if (HamSel<H>::kSameAlpha) amy = amx;
+    if constexpr (GF) {
+      amx = fmaxf(fmaxf(amx + 1.0f, amy - 1.0f), 0.0f);
+      amy = amx;
+    } else if (HamSel<H>::kSameAlpha) {
+      amy = amx;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       amx = fmaxf(amx, __shfl_xor_sync(0xffffffffu, amx, o));
@@ -644,7 +672,7 @@ __global__ void __launch_bounds__(Geo2D<TXv>::NT, Geo2D<TXv>::MINB)
         }
       }
     }
-    amx = amy = 0.0f;
+    amx = amy = A0;
     nfin = 0.0f;
     run_tiles = 0;
     __syncthreads();  // raw[buf], dX, su, s_info[buf] are free for the next tile
